@@ -1,0 +1,395 @@
+"""Throughput of the cryoSplat splatting path on B300: fwd+bwd particle images/s.
+
+Workload (default): D = 256 pixels, N = 100,000 Gaussians, a batch of 128 particles with
+their own poses and defocus (the D = 256 / N = 100k volume of the mixed-batch
+configuration), seeded synthetic inputs shaped like the paper's data.  One step =
+project -> bin/sort -> render -> CTF -> loss -> CTF adjoint -> render backward -> Adam over
+the whole batch.
+
+Printed (rank 0, one JSON line): the batched, fused form's images/s as ``value``; the plain
+form (one particle per launch sequence, batch size 1 as in the paper) on the same GPU; an
+end-to-end figure through the public API with host buffers; the roofline of the dominant
+kernel against the SFU ex2 peak; the FP64 oracle timed on the host cores as a CPU
+baseline; SM clocks sampled during the timed region.
+
+``--impl reference`` times the FP64 oracle itself on the host cores (the slow reference
+arm), on the same config and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2508_04929_b300 import synth  # noqa: E402
+
+METRIC = "fwd+bwd particle images/s at D=256,N=100k vs plain form; % of SFU-exp roofline"
+UNIT = "images/s"
+SM_COUNT = 148
+EX2_PER_CLK_PER_SM = 32  # measured on B300 by a throughput microbenchmark
+SM_MAX_MHZ = 2032.0
+CTF_SNR = 0.05
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--D", type=int, default=256)
+    p.add_argument("--N", type=int, default=100_000)
+    p.add_argument("--B", type=int, default=128)
+    p.add_argument("--tile", type=int, default=0, help="0 = autotune")
+    p.add_argument("--chunk", type=int, default=0, help="0 = autotune")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--cpu-sample", type=int, default=0, help="images in the CPU sample (0 = one per core, max 16)")
+    return p.parse_args()
+
+
+def workload(args):
+    return {"workload": f"D={args.D},N={args.N},B={args.B} synthetic particles (uniform-ball centres, "
+                        f"log-uniform 0.5-3 px scales, random rotations/poses, defocus 1-3 um)",
+            "D": args.D, "N": args.N, "batch": args.B, "seed": 0,
+            "l2": "inputs larger than L2 (records and gradient partials ~0.8 GB per step)"}
+
+
+def make_inputs(args, seed=0):
+    rng = synth.rng_for(seed)
+    th = synth.random_gaussians(args.N, args.D, rng)
+    Ws = synth.random_poses(args.B, rng).reshape(args.B, 9)
+    ctf = synth.random_ctf(args.B, rng)
+    th_gt = synth.random_gaussians(args.N, args.D, rng)
+    return th, Ws, ctf, th_gt, rng
+
+
+# ---------------------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle, one particle per process (spawned before CUDA starts)
+# ---------------------------------------------------------------------------------------
+def _oracle_image(payload):
+    import oracle as O
+    th, W, ctf_row, Y, D = payload
+    t0 = time.perf_counter()
+    O.forward_backward(th, W[None].reshape(1, 3, 3), D, Y[None], ctf_row[None])
+    return time.perf_counter() - t0
+
+
+def start_cpu_pool(n):
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    return cf.ProcessPoolExecutor(max_workers=n, mp_context=mp.get_context("spawn"))
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_cpu_sample(pool, th, Ws, ctf, Y, D, n):
+    payloads = [(th, Ws[b], ctf[b], Y[b], D) for b in range(n)]
+    t0 = time.perf_counter()
+    per = list(pool.map(_oracle_image, payloads))
+    wall = time.perf_counter() - t0
+    return wall, per
+
+
+# ---------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            time.sleep(0.25)
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], SM_MAX_MHZ, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------
+# the reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------------------
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    th, Ws, ctf, th_gt, rng = make_inputs(args)
+    Y = synth.smooth_field(args.B, args.D, rng, scale=1.0)  # stand-in observed images (cost is data independent)
+    cores = cpu_cores()
+    n = args.cpu_sample or min(cores, 16)
+    pool = start_cpu_pool(min(n, cores))
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        run_cpu_sample(pool, th, Ws, ctf, Y, args.D, min(n, args.B))
+    times = []
+    for _ in range(args.steps):
+        wall, _ = run_cpu_sample(pool, th, Ws, ctf, Y, args.D, min(n, args.B))
+        times.append(wall)
+    pool.shutdown()
+    tot = sum(times)
+    imgs = min(n, args.B) * args.steps
+    v = imgs / tot
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload(args),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": min(n, cores), "kind": "oracle",
+                             "sample": f"{min(n, args.B)} of the {args.B} particles per step, one per process"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    cores = cpu_cores()
+    want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    n_cpu = args.cpu_sample or min(cores, 16)
+    pool = start_cpu_pool(min(n_cpu, cores)) if want_cpu else None  # before the first CUDA call
+
+    import torch
+    from paper_2508_04929_b300 import build
+    build.build()
+    from paper_2508_04929_b300 import _lib as L
+    from paper_2508_04929_b300.splat import Splatter
+    from paper_2508_04929_b300 import autotune
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    th, Ws, ctf, th_gt, rng = make_inputs(args, seed=rank)
+    t = torch.from_numpy(th).to(dev)
+    W = torch.from_numpy(Ws).to(dev)
+    C = torch.from_numpy(ctf).to(dev)
+
+    # observed images: clean CTF images of a ground-truth GMM (rendered by this path) + noise
+    gt = Splatter(args.D, args.N, args.B, tile=16, chunk=128, device=dev)
+    tg = torch.from_numpy(th_gt).to(dev)
+    _, Xgt = gt.forward(tg, W, C)
+    sig = math.sqrt(float(Xgt.double().var()) / CTF_SNR)
+    gen = torch.Generator(device=dev).manual_seed(1234 + rank)
+    Y = (Xgt + sig * torch.randn(Xgt.shape, device=dev, generator=gen)).contiguous()
+    gt.close()
+    del gt, tg, Xgt
+
+    tile, chunk = args.tile, args.chunk
+    tune = None
+    if tile == 0 or chunk == 0:
+        tune = autotune.tune(args.D, args.N, args.B, t, W, C, Y, device=dev,
+                             tiles=(tile,) if tile else (8, 16, 32), chunks=(chunk,) if chunk else (64, 128, 256))
+        tile, chunk = tune["tile"], tune["chunk"]
+
+    sp = Splatter(args.D, args.N, args.B, tile=tile, chunk=chunk, device=dev)
+    dth = torch.zeros_like(t)
+    m = torch.zeros_like(t)
+    v = torch.zeros_like(t)
+    theta = t.clone()
+    # size the pair buffer once (host sync), then run without syncs
+    sp.forward(theta, W, C, grow=True)
+    sp.pairs = torch.empty(int((int(sp.n_pairs.item()) & 0xFFFFFFFF) * 1.3) + 4096, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    ev = {k: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for k in ("fwd", "bwd")}
+    kt = {"fwd": [], "bwd": []}
+    step_no = [0]
+
+    def step(timed=False):
+        dth.zero_()
+        sp.project(theta, W)
+        sp.bin_sort(grow=False)
+        if timed:
+            ev["fwd"][0].record(stream)
+        sp.render()
+        if timed:
+            ev["fwd"][1].record(stream)
+        sp.apply_ctf(sp.Q, C, sp.X)
+        sp.loss_grad(sp.X, Y)
+        sp.apply_ctf(sp.dX, C, sp.dQ)
+        if timed:
+            ev["bwd"][0].record(stream)
+        sp.backward(theta, W, sp.dQ, dth)
+        if timed:
+            ev["bwd"][1].record(stream)
+        step_no[0] += 1
+        L.gs_step(theta, dth, m, v, step_no[0])
+        if timed:
+            torch.cuda.synchronize()
+            kt["fwd"].append(ev["fwd"][0].elapsed_time(ev["fwd"][1]))
+            kt["bwd"].append(ev["bwd"][0].elapsed_time(ev["bwd"][1]))
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    st = sp.status()
+    # algorithmic work: Gaussian-pixel evaluations inside the support boxes of this batch
+    box = sp.proj.view(torch.int16).view(args.B, args.N, 16)[:, :, 12:16].to(torch.int64)
+    area = ((box[..., 1] - box[..., 0] + 1).clamp(min=0) * (box[..., 3] - box[..., 2] + 1).clamp(min=0))
+    e_alg = int(area.sum())
+    n_pairs = int(sp.n_pairs.item()) & 0xFFFFFFFF
+
+    # --- timed region: batched form (kernel-level per-call events in a second pass) ---
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_total = e0.elapsed_time(e1)
+        for _ in range(min(args.steps, 5)):
+            step(timed=True)
+    if dist is not None:
+        tt = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms_step = ms_total / args.steps
+    value = world * args.B / (ms_step * 1e-3)
+    t_fwd = statistics.median(kt["fwd"])
+    t_bwd = statistics.median(kt["bwd"])
+
+    # --- plain form: one particle per launch sequence, batch size 1, Adam per image ---
+    plain = None
+    if not args.no_plain:
+        p1 = Splatter(args.D, args.N, 1, tile=16, chunk=128, device=dev)
+        th1 = t.clone()
+        m1, v1, g1 = torch.zeros_like(t), torch.zeros_like(t), torch.zeros_like(t)
+        for b in range(2):
+            g1.zero_()
+            p1.forward_backward(th1, W[b:b + 1], C[b:b + 1], Y[b:b + 1], g1, grow=True)
+        torch.cuda.synchronize()
+        nimg = min(args.B, 64)
+        s0 = time.perf_counter()
+        for b in range(nimg):
+            g1.zero_()
+            p1.forward_backward(th1, W[b:b + 1], C[b:b + 1], Y[b:b + 1], g1, grow=True)
+            L.gs_step(th1, g1, m1, v1, b + 1)
+        torch.cuda.synchronize()
+        plain = nimg / (time.perf_counter() - s0)
+        p1.close()
+
+    # --- end to end through the public API with host buffers ---
+    Yh = Y.cpu().pin_memory()
+    Wh = W.cpu().pin_memory()
+    Ch = C.cpu().pin_memory()
+    Yd, Wd, Cd = torch.empty_like(Y), torch.empty_like(W), torch.empty_like(C)
+    lossh = torch.empty(args.B, dtype=torch.float32).pin_memory()
+    h2d = Yh.numel() * 4 + Wh.numel() * 4 + Ch.numel() * 4
+    d2h = lossh.numel() * 4
+    torch.cuda.synchronize()
+    s0 = time.perf_counter()
+    for i in range(args.steps):
+        Yd.copy_(Yh, non_blocking=True)
+        Wd.copy_(Wh, non_blocking=True)
+        Cd.copy_(Ch, non_blocking=True)
+        dth.zero_()
+        sp.forward_backward(theta, Wd, Cd, Yd, dth, grow=False)
+        L.gs_step(theta, dth, m, v, step_no[0] + i + 1)
+        lossh.copy_(sp.loss[: args.B], non_blocking=True)
+        torch.cuda.synchronize()
+    e2e = world * args.B * args.steps / (time.perf_counter() - s0)
+
+    cpu = None
+    if pool is not None:
+        Ynp = Y.cpu().numpy()
+        n = min(n_cpu, args.B)
+        wall, per = run_cpu_sample(pool, th, Ws, ctf, Ynp, args.D, n)
+        pool.shutdown()
+        cpu = {"value": n / wall, "unit": UNIT, "cores": min(n_cpu, cores), "kind": "oracle",
+               "sample": f"{n} of the {args.B} particles (same inputs), one particle per process, "
+                         f"median {statistics.median(per):.1f} s per particle"}
+
+    peak_exp = SM_COUNT * EX2_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6  # ex2 per second
+    dom = "bwd" if t_bwd >= t_fwd else "fwd"
+    t_dom = max(t_bwd, t_fwd)
+    achieved = e_alg / (t_dom * 1e-3)
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(workload(args), tile=tile, chunk=chunk, parallelism="replicas" if world > 1 else "single"),
+            "plain_form": {"value": plain, "unit": UNIT, "form": "one particle per launch sequence, Adam per image"},
+            "speedup_vs_plain": (value / world / plain) if plain else None,
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": 13 * args.steps,
+            "roofline": {"bound": "alu", "kernel": f"k_render_{dom}", "achieved": achieved / 1e9,
+                         "peak": peak_exp / 1e9, "unit": "Gex2/s", "frac": achieved / peak_exp, "traffic": None},
+            "fwd_bwd_splat": {"ms_fwd": t_fwd, "ms_bwd": t_bwd, "alg_evals_per_step": e_alg,
+                              "pairs_per_step": n_pairs,
+                              "frac_of_sfu_roofline": (2 * e_alg / ((t_fwd + t_bwd) * 1e-3)) / peak_exp},
+            "cpu_baseline": cpu, "clocks": clocks, "status": st,
+            "autotune": tune,
+        }
+        print(json.dumps(line), flush=True)
+    sp.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

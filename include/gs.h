@@ -1,0 +1,195 @@
+/*
+ * gs.h -- C-ABI of the B300 (sm_103a) cryoSplat orthographic splatting path.
+ *
+ * The operations follow arXiv 2508.04929 ("CryoSplat: Gaussian Splatting for Cryo-EM
+ * Homogeneous Reconstruction"): Algorithm 2 (Rasterize), App. A.2 Eqs. 12-21 (projection,
+ * FFT-aligned pixel grid, CTF, gradients), Sec. 3.3.5 (loss) and Sec. 4.1 (Adam).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All array pointers are DEVICE pointers owned by the caller, except where a comment
+ *   says "host".  The library never allocates device memory: scratch space is the
+ *   caller's workspace (gs_workspace_size).  cuFFT plans are created by gs_fft_create.
+ * - Every call is asynchronous and stream-ordered on `stream` (cudaStream_t; NULL is the
+ *   legacy default stream).  Launch failures are reported as GS_ECUDA.  Conditions found
+ *   on the device (non-finite parameters, pair-buffer overflow) are recorded as bits of a
+ *   status word kept at the start of the workspace; read it with gs_read_status.
+ * - Layouts are row-major and dense.  Floating point is FP32.  Model units: the box spans
+ *   [-E, E] (E = 0.5), so one pixel is h = 2E / D.
+ * - theta[N * 11] per Gaussian = [mu_x, mu_y, mu_z, s_x, s_y, s_z, q_w, q_x, q_y, q_z, A]
+ *   in raw form: A = softplus(theta[10]), s = softplus(theta[3..5]), q normalized
+ *   (Sec. 3.3.1).  W[B * 9] is the row-major pose of each particle, mu_dot = W mu
+ *   (Sec. 3.3.2 Eq. 6; no in-plane translation on this path, Sec. 4.1).
+ * - Pixel (i, j) of a D x D image samples the continuous image at
+ *   ((j - floor(D/2)) h, -(i - floor(D/2)) h): App. A.2 Eq. 13 (FFT-aligned origin, y flip).
+ * - Support: Gaussian g contributes to the pixels of its clipped k-sigma box
+ *   [ceil(cx - rx), floor(cx + rx)] x [ceil(cy - ry), floor(cy + ry)] with
+ *   rx = k sqrt(Sigma~xx) / h, ry = k sqrt(Sigma~yy) / h (k = cutoff_sigma).  The box is
+ *   computed in FP32 with a fixed sequence of correctly rounded operations (documented in
+ *   gs_project) so that it is reproducible; it does not depend on the tile size.
+ *
+ * Return codes: GS_OK on success; GS_EINVAL for a bad argument (null pointer with a
+ * non-zero size, misaligned pointer, size out of range, unsupported tile); GS_ENOSPC when
+ * a caller-provided buffer is too small (the needed size is reported where an argument
+ * allows it); GS_ECUDA when a CUDA or cuFFT call fails.
+ */
+#ifndef GS_H_
+#define GS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* gs_stream_t; /* = cudaStream_t */
+
+enum {
+  GS_OK = 0,
+  GS_EINVAL = 1,
+  GS_ENOSPC = 2,
+  GS_ECUDA = 3,
+};
+
+/* Bits of the device status word (gs_read_status). */
+enum {
+  GS_STATUS_NONFINITE = 1, /* a Gaussian had a non-finite parameter or box; it was skipped */
+  GS_STATUS_OVERFLOW = 2,  /* more tile pairs than pair_capacity; extra pairs were dropped */
+};
+
+typedef struct gs_config {
+  int D;              /* image side in pixels, 1..4096 */
+  float E;            /* half extent of the box in model units (the paper uses 0.5) */
+  int tile;           /* tile side in pixels: 8, 16 or 32 (App. C.2 uses 16) */
+  int chunk;          /* Gaussian records staged per shared-memory chunk: 32..512, multiple of 32 */
+  float cutoff_sigma; /* k of the k-sigma support box (3) */
+  int reduction;      /* loss per image: 0 = sum of squares (Sec. 3.3.5), 1 = mean over pixels */
+} gs_config;
+
+/* Projected record of one (particle, Gaussian) pair: 32 bytes, 16-byte aligned.
+ * The splat value at pixel (i, j) is w * 2^(ca dx^2 + cb dx dy + cc dy^2) with
+ * dx = j - cx, dy = i - cy (pixel units); w = A / (2 pi sqrt(det Sigma~)) in model units.
+ * [x0, x1] x [y0, y1] is the clipped support box (empty when x0 > x1). */
+typedef struct gs_record {
+  float cx, cy;
+  float ca, cb, cc;
+  float w;
+  int16_t x0, x1, y0, y1;
+} gs_record;
+
+/* Opaque pair of batched cuFFT plans (R2C and C2R over B images of D x D). */
+typedef struct gs_fft {
+  int r2c;           /* cufftHandle */
+  int c2r;           /* cufftHandle */
+  int D;
+  int B;
+  size_t work_bytes; /* cuFFT work area needed (placed inside the gs workspace) */
+} gs_fft;
+
+/* ---------------------------------------------------------------------------------------
+ * Sizes and set-up
+ * ------------------------------------------------------------------------------------- */
+
+/* Number of tiles per image, ceil(D / tile)^2, into *n.  GS_EINVAL on a bad config. */
+int gs_tiles_per_image(const gs_config* cfg, int* n);
+
+/* Workspace bytes for batches of up to B particles and N Gaussians with the given cuFFT
+ * work area (gs_fft.work_bytes, 0 if gs_apply_ctf is not used).  The workspace holds the
+ * status word, the activated Gaussians, the binning histograms, the per-(particle,
+ * Gaussian) gradient partials, the half spectra and the cuFFT work area.  It must be
+ * 256-byte aligned; its contents need no initialization. */
+int gs_workspace_size(const gs_config* cfg, int B, int N, size_t fft_work_bytes, size_t* bytes);
+
+/* Create batched cuFFT plans for B images of D x D (automatic work-area allocation off;
+ * the work area lives in the gs workspace).  Host-side call; cuFFT allocates its own plan
+ * state.  Release with gs_fft_destroy. */
+int gs_fft_create(int D, int B, gs_fft* fft);
+int gs_fft_destroy(gs_fft* fft);
+
+/* Copy the device status word to *status (host) and wait for `stream`.  If `clear` is
+ * non-zero the word is reset to 0 afterwards (stream-ordered). */
+int gs_read_status(const void* ws, gs_stream_t stream, int clear, int* status);
+
+/* Reset the status word to 0 (stream-ordered, asynchronous). */
+int gs_clear_status(void* ws, gs_stream_t stream);
+
+/* ---------------------------------------------------------------------------------------
+ * The path (Algorithm 1 body: Rasterize -> ApplyCTF -> Loss -> backprop -> Adam)
+ * ------------------------------------------------------------------------------------- */
+
+/* BuildGaussians + ViewingTransform + Projection (Algorithm 2; Sec. 3.3.1-3.3.3, Eqs. 5, 6,
+ * 8; App. A.2 Eqs. 12-13).
+ * theta[N*11] raw parameters, W[B*9] poses -> proj[B*N] records (gs_record, particle-major:
+ * proj[b*N + g]).  Also fills the activated-Gaussian table in `ws` used by gs_render_bwd.
+ * The support box is computed in FP32 in this order, every operation correctly rounded:
+ *   s = fp32(softplus(s_raw) in FP64);  n = sqrt(((qw*qw + qx*qx) + qy*qy) + qz*qz);
+ *   (w,x,y,z) = q / n;  R from (w,x,y,z) with the pairwise products formed first,
+ *   e.g. R00 = 1 - 2*(y*y + z*z), R01 = 2*(x*y - w*z), R02 = 2*(x*z + w*y), ...;
+ *   M[k][m] = R[k][m] * s[m];  V[a][m] = (W[a][0]*M[0][m] + W[a][1]*M[1][m]) + W[a][2]*M[2][m];
+ *   Sxx = (V00^2 + V01^2) + V02^2;  Syy = (V10^2 + V11^2) + V12^2;
+ *   mx = (W00 mu_x + W01 mu_y) + W02 mu_z;  my = (W10 mu_x + W11 mu_y) + W12 mu_z;
+ *   inv_h = D / (2E);  cx = mx * inv_h + floor(D/2);  cy = floor(D/2) - my * inv_h;
+ *   rx = k * (sqrt(Sxx) * inv_h);  ry = k * (sqrt(Syy) * inv_h).
+ * Gaussians with a non-finite parameter or box get an empty box and set
+ * GS_STATUS_NONFINITE.  Pointers: theta, W 4-byte aligned; proj 16-byte aligned. */
+int gs_project(const gs_config* cfg, const float* theta, int N, const float* W, int B,
+               gs_record* proj, void* ws, size_t ws_bytes, gs_stream_t stream);
+
+/* CreateTiles + DuplicateWithKeys + SortByKeys + IdentifyTileRanges (Algorithm 2).
+ * Instantiates every Gaussian in every tile its support box touches and orders the
+ * instances by the key (particle, tile, Gaussian): a stable counting sort on the tile
+ * digit of Gaussians emitted in index order, i.e. the last pass of an LSD radix sort
+ * keyed on (tile, Gaussian).
+ * Outputs: pair_gauss[pair_capacity] Gaussian index of every instance;
+ * tile_ranges[B * T * 2] absolute [start, end) of each (particle, tile) in pair_gauss
+ * (T = gs_tiles_per_image); *n_pairs (device uint32) the number of instances needed.
+ * If that exceeds pair_capacity the extra instances are dropped, the ranges are clipped
+ * to pair_capacity and GS_STATUS_OVERFLOW is set.  Requires ceil(D/tile) <= 64 and
+ * N * T < 2^32 (GS_EINVAL otherwise). */
+int gs_bin_sort(const gs_config* cfg, const gs_record* proj, int B, int N, void* ws,
+                size_t ws_bytes, uint32_t* pair_gauss, size_t pair_capacity,
+                uint32_t* tile_ranges, uint32_t* n_pairs, gs_stream_t stream);
+
+/* SumSplats (Algorithm 2; App. A.2 Eq. 15 at the Eq. 13 pixel centres): additive
+ * accumulation, no alpha compositing (Sec. 3.3.4).
+ * Q[B * D * D] = sum over each pixel's tile list of w * 2^(quadratic) inside the support
+ * box.  Every pixel is written (zero where nothing contributes). */
+int gs_render_fwd(const gs_config* cfg, const gs_record* proj, int N, const uint32_t* pair_gauss,
+                  const uint32_t* tile_ranges, int B, float* Q, gs_stream_t stream);
+
+/* ApplyCTF (App. A.2 Eq. 14): out = F^-1(H_hat . F(in)) per image, with
+ * H_hat(k) = -(sqrt(1 - w^2) sin chi + w cos chi), chi = pi lambda df |k|^2 -
+ * (pi/2) Cs lambda^3 |k|^4 and the relativistic electron wavelength lambda.
+ * ctf[B * 5] per image = (defocus_A, kV, Cs_mm, amplitude_contrast, pixel_size_A).
+ * H_hat is real and even, so the operator is self-adjoint: the same call applies the
+ * adjoint for the backward pass.  in and out may not alias.  Uses cuFFT (fft must have
+ * been created for this D and B) and the spectrum / work area inside ws. */
+int gs_apply_ctf(const gs_config* cfg, const float* in, const float* ctf, int B, float* out,
+                 const gs_fft* fft, void* ws, size_t ws_bytes, gs_stream_t stream);
+
+/* Loss (Sec. 3.3.5): loss[b] = sum_p (X - Y)^2 (reduction 0) or its mean over pixels
+ * (reduction 1); dLdX = dloss[b]/dX (= 2 (X - Y) times the reduction scale).
+ * dLdX may be NULL (loss only). */
+int gs_loss(const gs_config* cfg, const float* X, const float* Y, int B, float* loss,
+            float* dLdX, gs_stream_t stream);
+
+/* Backward of Rasterize (App. A.2 Eqs. 16-21; grad_mu = W^T [grad_mu_tilde; 0]; the s, q
+ * chain through Sigma = (R S)(R S)^T; softplus derivatives).  Accumulates (+=) dL/dtheta
+ * into dtheta[N * 11] summed over the B particles; the caller zeroes it first.  proj,
+ * pair_gauss and tile_ranges are the outputs of gs_project / gs_bin_sort for the same
+ * theta and W, and ws must still hold what gs_project wrote. */
+int gs_render_bwd(const gs_config* cfg, const float* theta, int N, const float* W, int B,
+                  const gs_record* proj, const uint32_t* pair_gauss, const uint32_t* tile_ranges,
+                  const float* dLdQ, float* dtheta, void* ws, size_t ws_bytes, gs_stream_t stream);
+
+/* Adam step with one learning rate for all parameters (Sec. 4.1):
+ * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; theta -= lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps).
+ * t >= 1 counts steps.  n = 11 N. */
+int gs_step(float* theta, const float* dtheta, float* m, float* v, int n, int t, float lr,
+            float beta1, float beta2, float eps, gs_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_H_ */

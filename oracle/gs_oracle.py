@@ -43,7 +43,7 @@ __all__ = [
     "softplus", "sigmoid", "quat_to_rot", "quat_to_rot_jacobian",
     "build_gaussians", "viewing_transform", "projection", "splat",
     "pixel_centres", "support_fp32", "render", "render_one",
-    "tile_pairs", "electron_wavelength", "ctf_radial", "ctf_image", "dft2", "idft2",
+    "tile_pairs", "tile_counts", "electron_wavelength", "ctf_radial", "ctf_image", "dft2", "idft2",
     "apply_ctf", "apply_ctf_adjoint", "loss", "backward", "adam_step",
     "forward_backward",
 ]
@@ -172,7 +172,7 @@ def _sp32(x32):
     return softplus(np.asarray(x32, dtype=F64)).astype(F32)
 
 
-def support_fp32(theta, W, D, E=0.5, cutoff=3.0):
+def support_fp32(theta, W, D, E=0.5, cutoff=3.0, centres=False):
     """Clipped k-sigma pixel box of every Gaussian for one pose, in FP32.
 
     Reading of the support rule (the paper inherits 3-sigma culling from 3DGS, Sec. 3.3.4,
@@ -195,7 +195,8 @@ def support_fp32(theta, W, D, E=0.5, cutoff=3.0):
 
     theta: [N, 11] (FP32 values), W: [3, 3] (FP32 values).
     Returns int64 arrays x0, x1, y0, y1 (inclusive; empty when x0 > x1 or y0 > y1) and a
-    bool array ``bad`` marking excluded non-finite Gaussians."""
+    bool array ``bad`` marking excluded non-finite Gaussians; with ``centres`` also the
+    FP32 centre (c_x, c_y) in pixel units."""
     th = np.asarray(theta, dtype=F32).reshape(-1, 11)
     Wf = np.asarray(W, dtype=F32).reshape(3, 3)
     n = th.shape[0]
@@ -241,6 +242,8 @@ def support_fp32(theta, W, D, E=0.5, cutoff=3.0):
     y0 = np.where(bad, 1, np.nan_to_num(y0f, nan=1)).astype(np.int64)
     y1 = np.where(bad, 0, np.nan_to_num(y1f, nan=0)).astype(np.int64)
     assert x0.shape == (n,)
+    if centres:
+        return x0, x1, y0, y1, bad, cx, cy
     return x0, x1, y0, y1, bad
 
 
@@ -305,6 +308,23 @@ def tile_pairs(theta, Ws, D, tile, E=0.5, cutoff=3.0):
     ranges[:, :, 0] = start
     ranges[:, :, 1] = start + counts
     return pair_gauss, ranges
+
+
+def tile_counts(theta, Ws, D, tile, E=0.5, cutoff=3.0):
+    """Instances per (particle, tile) of ``tile_pairs`` (counts[B, T]), without listing them:
+    every Gaussian adds one to each tile of its support box's tile rectangle."""
+    Ws = np.asarray(Ws).reshape(-1, 3, 3)
+    nt = -(-D // tile)
+    counts = np.zeros((Ws.shape[0], nt * nt), dtype=np.int64)
+    for b in range(Ws.shape[0]):
+        x0, x1, y0, y1, _ = support_fp32(theta, Ws[b], D, E, cutoff)
+        ok = (x0 <= x1) & (y0 <= y1)
+        tx0, tx1, ty0, ty1 = x0[ok] // tile, x1[ok] // tile, y0[ok] // tile, y1[ok] // tile
+        for oy in range(int((ty1 - ty0).max(initial=-1)) + 1):
+            for ox in range(int((tx1 - tx0).max(initial=-1)) + 1):
+                m = (ty0 + oy <= ty1) & (tx0 + ox <= tx1)
+                np.add.at(counts[b], (ty0[m] + oy) * nt + tx0[m] + ox, 1)
+    return counts
 
 
 # ----------------------------------------------------------------------------------------

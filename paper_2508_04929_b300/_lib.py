@@ -1,0 +1,166 @@
+"""ctypes binding of libgs.so (include/gs.h).  Argument marshalling only.
+
+Every function here has the name of the C entry point it calls and takes torch tensors
+(device memory) plus plain Python values; it passes their data pointers and the current
+CUDA stream to the library and raises ``GsError`` on a non-zero return code.  There is no
+fallback: if libgs.so is missing or fails to load, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgs.so")
+
+GS_OK, GS_EINVAL, GS_ENOSPC, GS_ECUDA = 0, 1, 2, 3
+GS_STATUS_NONFINITE, GS_STATUS_OVERFLOW = 1, 2
+RECORD_BYTES = 32
+
+_ERR = {GS_EINVAL: "invalid argument", GS_ENOSPC: "buffer too small", GS_ECUDA: "CUDA/cuFFT failure"}
+
+
+class GsError(RuntimeError):
+    def __init__(self, name, rc):
+        super().__init__(f"{name} failed: {_ERR.get(rc, rc)} (code {rc})")
+        self.rc = rc
+
+
+class GsConfig(ctypes.Structure):
+    _fields_ = [("D", ctypes.c_int), ("E", ctypes.c_float), ("tile", ctypes.c_int), ("chunk", ctypes.c_int),
+                ("cutoff_sigma", ctypes.c_float), ("reduction", ctypes.c_int)]
+
+
+class GsFFT(ctypes.Structure):
+    _fields_ = [("r2c", ctypes.c_int), ("c2r", ctypes.c_int), ("D", ctypes.c_int), ("B", ctypes.c_int),
+                ("work_bytes", ctypes.c_size_t)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libgs.so not built ({LIB_PATH}); run python -m paper_2508_04929_b300.build")
+    return ctypes.CDLL(LIB_PATH)
+
+
+lib = _load()
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_F = ctypes.c_float
+_S = ctypes.c_size_t
+_CFG = ctypes.POINTER(GsConfig)
+_SIGS = {
+    "gs_tiles_per_image": [_CFG, ctypes.POINTER(_I)],
+    "gs_workspace_size": [_CFG, _I, _I, _S, ctypes.POINTER(_S)],
+    "gs_fft_create": [_I, _I, ctypes.POINTER(GsFFT)],
+    "gs_fft_destroy": [ctypes.POINTER(GsFFT)],
+    "gs_read_status": [_P, _P, _I, ctypes.POINTER(_I)],
+    "gs_clear_status": [_P, _P],
+    "gs_project": [_CFG, _P, _I, _P, _I, _P, _P, _S, _P],
+    "gs_bin_sort": [_CFG, _P, _I, _I, _P, _S, _P, _S, _P, _P, _P],
+    "gs_render_fwd": [_CFG, _P, _I, _P, _P, _I, _P, _P],
+    "gs_apply_ctf": [_CFG, _P, _P, _I, _P, ctypes.POINTER(GsFFT), _P, _S, _P],
+    "gs_loss": [_CFG, _P, _P, _I, _P, _P, _P],
+    "gs_render_bwd": [_CFG, _P, _I, _P, _I, _P, _P, _P, _P, _P, _P, _S, _P],
+    "gs_step": [_P, _P, _P, _P, _I, _I, _F, _F, _F, _F, _P],
+}
+for _name, _args in _SIGS.items():
+    _fn = getattr(lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = ctypes.c_int
+
+EXPORTED = tuple(_SIGS)
+
+
+def _check(name, rc):
+    if rc != GS_OK:
+        raise GsError(name, rc)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def config(D, E=0.5, tile=16, chunk=128, cutoff_sigma=3.0, reduction=0) -> GsConfig:
+    return GsConfig(int(D), float(E), int(tile), int(chunk), float(cutoff_sigma), int(reduction))
+
+
+def gs_tiles_per_image(cfg: GsConfig) -> int:
+    n = _I()
+    _check("gs_tiles_per_image", lib.gs_tiles_per_image(ctypes.byref(cfg), ctypes.byref(n)))
+    return n.value
+
+
+def gs_workspace_size(cfg: GsConfig, B: int, N: int, fft_work_bytes: int = 0) -> int:
+    n = _S()
+    _check("gs_workspace_size", lib.gs_workspace_size(ctypes.byref(cfg), B, N, fft_work_bytes, ctypes.byref(n)))
+    return n.value
+
+
+def gs_fft_create(D: int, B: int) -> GsFFT:
+    f = GsFFT()
+    _check("gs_fft_create", lib.gs_fft_create(D, B, ctypes.byref(f)))
+    return f
+
+
+def gs_fft_destroy(f: GsFFT) -> None:
+    _check("gs_fft_destroy", lib.gs_fft_destroy(ctypes.byref(f)))
+
+
+def gs_read_status(ws, clear=True, stream=None) -> int:
+    st = _I()
+    _check("gs_read_status", lib.gs_read_status(_ptr(ws), _stream(stream), int(clear), ctypes.byref(st)))
+    return st.value
+
+
+def gs_clear_status(ws, stream=None) -> None:
+    _check("gs_clear_status", lib.gs_clear_status(_ptr(ws), _stream(stream)))
+
+
+def gs_project(cfg, theta, W, proj, ws, stream=None) -> None:
+    N, B = theta.shape[0], W.shape[0]
+    _check("gs_project", lib.gs_project(ctypes.byref(cfg), _ptr(theta), N, _ptr(W), B, _ptr(proj), _ptr(ws),
+                                        ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def gs_bin_sort(cfg, proj, B, N, ws, pair_gauss, tile_ranges, n_pairs, stream=None) -> None:
+    cap = 0 if pair_gauss is None else pair_gauss.numel()
+    _check("gs_bin_sort", lib.gs_bin_sort(ctypes.byref(cfg), _ptr(proj), B, N, _ptr(ws),
+                                          ws.numel() * ws.element_size(), _ptr(pair_gauss), cap,
+                                          _ptr(tile_ranges), _ptr(n_pairs), _stream(stream)))
+
+
+def gs_render_fwd(cfg, proj, N, pair_gauss, tile_ranges, B, Q, stream=None) -> None:
+    _check("gs_render_fwd", lib.gs_render_fwd(ctypes.byref(cfg), _ptr(proj), N, _ptr(pair_gauss),
+                                              _ptr(tile_ranges), B, _ptr(Q), _stream(stream)))
+
+
+def gs_apply_ctf(cfg, inp, ctf, out, fft, ws, stream=None) -> None:
+    B = inp.shape[0]
+    _check("gs_apply_ctf", lib.gs_apply_ctf(ctypes.byref(cfg), _ptr(inp), _ptr(ctf), B, _ptr(out),
+                                            ctypes.byref(fft), _ptr(ws), ws.numel() * ws.element_size(),
+                                            _stream(stream)))
+
+
+def gs_loss(cfg, X, Y, loss, dLdX=None, stream=None) -> None:
+    _check("gs_loss", lib.gs_loss(ctypes.byref(cfg), _ptr(X), _ptr(Y), X.shape[0], _ptr(loss), _ptr(dLdX),
+                                  _stream(stream)))
+
+
+def gs_render_bwd(cfg, theta, W, proj, pair_gauss, tile_ranges, dLdQ, dtheta, ws, stream=None) -> None:
+    N, B = theta.shape[0], W.shape[0]
+    _check("gs_render_bwd", lib.gs_render_bwd(ctypes.byref(cfg), _ptr(theta), N, _ptr(W), B, _ptr(proj),
+                                              _ptr(pair_gauss), _ptr(tile_ranges), _ptr(dLdQ), _ptr(dtheta),
+                                              _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def gs_step(theta, dtheta, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None) -> None:
+    _check("gs_step", lib.gs_step(_ptr(theta), _ptr(dtheta), _ptr(m), _ptr(v), theta.numel(), int(t), float(lr),
+                                  float(beta1), float(beta2), float(eps), _stream(stream)))

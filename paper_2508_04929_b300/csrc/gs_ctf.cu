@@ -1,0 +1,118 @@
+// ApplyCTF (App. A.2 Eq. 14), the loss (Sec. 3.3.5) and Adam (Sec. 4.1).
+//
+// k_ctf_mul multiplies the R2C half spectrum of each image by H_hat / D^2.  H_hat depends
+// on the integer n = fx^2 + fy^2 only: chi / pi = alpha n - beta n^2 with per-image
+// constants alpha = lambda df / (D apix)^2 and beta = Cs lambda^3 / (2 (D apix)^4), formed
+// once per CTA in FP64.  The phase is reduced modulo 2 exactly (the product alpha_hi * n is
+// split into its rounded value and its exact FMA remainder), so sinpi / cospi see an
+// argument accurate to ~1e-7 even where chi reaches hundreds of radians.
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+__global__ void k_ctf_mul(float2* __restrict__ spec, const float* __restrict__ ctf, int D) {
+  const int b = blockIdx.y;
+  const int W2 = D / 2 + 1;
+  __shared__ float cst[6];
+  if (threadIdx.x == 0) {
+    const double df = ctf[b * 5 + 0], kv = ctf[b * 5 + 1], cs = ctf[b * 5 + 2] * 1e7, w = ctf[b * 5 + 3],
+                 apix = ctf[b * 5 + 4];
+    const double V = kv * 1e3;
+    const double lam = 12.2643 / sqrt(V * (1.0 + 0.978466e-6 * V));
+    const double s2 = 1.0 / ((double)D * apix * (double)D * apix);
+    const double alpha = lam * df * s2;
+    const double beta = 0.5 * cs * lam * lam * lam * s2 * s2;
+    const float ahi = (float)alpha;
+    cst[0] = ahi;
+    cst[1] = (float)(alpha - (double)ahi);
+    cst[2] = (float)beta;
+    cst[3] = (float)sqrt(1.0 - w * w);
+    cst[4] = (float)w;
+    cst[5] = (float)(1.0 / ((double)D * (double)D));
+  }
+  __syncthreads();
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= D * W2) return;
+  const int l = idx / W2, m = idx - l * W2;
+  const int fy = l < (D + 1) / 2 ? l : l - D;
+  const float n = (float)(fy * fy + m * m);  // exact (< 2^24)
+  const float p = cst[0] * n;
+  const float perr = fmaf(cst[0], n, -p);  // exact remainder of alpha_hi * n
+  const float pred = p - 2.f * rintf(0.5f * p);  // exact: p mod 2 in [-1, 1]
+  const float q = cst[2] * n * n;
+  const float qred = q - 2.f * rintf(0.5f * q);
+  const float tt = (pred + perr + cst[1] * n) - qred;
+  float sp, cp;
+  sincospif(tt, &sp, &cp);
+  const float H = -(cst[3] * sp + cst[4] * cp) * cst[5];
+  float2* z = spec + (size_t)b * D * W2 + idx;
+  float2 v = *z;
+  v.x *= H;
+  v.y *= H;
+  *z = v;
+}
+
+__global__ void k_loss(const float* __restrict__ X, const float* __restrict__ Y, int P, float scale,
+                       float* __restrict__ loss, float* __restrict__ dLdX) {
+  const int b = blockIdx.x;
+  const float* x = X + (size_t)b * P;
+  const float* y = Y + (size_t)b * P;
+  float acc = 0.f;
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    const float r = x[p] - y[p];
+    acc = fmaf(r, r, acc);
+    if (dLdX) dLdX[(size_t)b * P + p] = 2.f * scale * r;
+  }
+  __shared__ float red[32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) loss[b] = v * scale;
+  }
+}
+
+__global__ void k_adam(float* __restrict__ th, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, int n, float lr, float b1, float b2, float eps, float c1, float c2) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    th[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_ctf_mul(const gs_config& cfg, float2* spec, const float* ctf, int B, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  const int D = cfg.D, cnt = D * (D / 2 + 1);
+  dim3 grid((cnt + 255) / 256, B);
+  k_ctf_mul<<<grid, 256, 0, s>>>(spec, ctf, D);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loss(const gs_config& cfg, const float* X, const float* Y, int B, float* loss, float* dLdX,
+                        cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  const int P = cfg.D * cfg.D;
+  const float scale = cfg.reduction == 1 ? 1.f / (float)P : 1.f;
+  k_loss<<<B, 512, 0, s>>>(X, Y, P, scale, loss, dLdX);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* theta, const float* g, float* m, float* v, int n, float lr, float b1, float b2,
+                        float eps, float c1, float c2, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int blocks = (n + 255) / 256;
+  if (blocks > 148 * 16) blocks = 148 * 16;
+  k_adam<<<blocks, 256, 0, s>>>(theta, g, m, v, n, lr, b1, b2, eps, c1, c2);
+  return cudaGetLastError();
+}
+
+}  // namespace gs

@@ -1,0 +1,103 @@
+// Internal definitions shared by the CUDA translation units of libgs (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gs.h"
+
+namespace gs {
+
+constexpr int kBinChunk = 2048;       // Gaussians per binning CTA (8 warps x 256, in order)
+constexpr int kBinWarps = 8;
+constexpr int kGaussStride = 20;      // floats per activated Gaussian in the workspace
+constexpr int kGradStride = 8;        // floats per (particle, Gaussian) gradient partial
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kInv2Pi = 0.15915494309189535f;
+
+// Layout of the activated-Gaussian table (one row of kGaussStride floats per Gaussian).
+enum GaussField {
+  kMu = 0,     // mu[3]
+  kM = 3,      // M = R diag(s), row-major [3][3]
+  kS = 12,     // s[3] (FP32, rounded once from the FP64 softplus)
+  kA = 15,     // A
+  kSprod = 16, // s0 s1 s2
+  kBad = 17,   // 1 if a parameter is not finite
+};
+
+// Workspace carve-up; every part 256-byte aligned.
+struct WsLayout {
+  size_t status, gauss, hist, tstart, ttotal, itotal, ibase, gacc, spec, fftwork, total;
+  int Tn, C, ntx;
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+inline WsLayout ws_layout(const gs_config& cfg, int B, int N, size_t fft_work) {
+  WsLayout L;
+  L.ntx = (cfg.D + cfg.tile - 1) / cfg.tile;
+  L.Tn = L.ntx * L.ntx;
+  L.C = (N + kBinChunk - 1) / kBinChunk;
+  if (L.C < 1) L.C = 1;
+  size_t o = 0;
+  L.status = o; o = align256(o + 256);
+  L.gauss = o; o = align256(o + sizeof(float) * kGaussStride * (size_t)N);
+  L.hist = o; o = align256(o + sizeof(uint32_t) * (size_t)B * L.C * L.Tn);
+  L.tstart = o; o = align256(o + sizeof(uint32_t) * (size_t)B * L.Tn);
+  L.ttotal = o; o = align256(o + sizeof(uint32_t) * (size_t)B * L.Tn);
+  L.itotal = o; o = align256(o + sizeof(uint32_t) * ((size_t)B + 1));
+  L.ibase = o; o = align256(o + sizeof(unsigned long long) * ((size_t)B + 1));
+  L.gacc = o; o = align256(o + sizeof(float) * kGradStride * (size_t)B * N);
+  L.spec = o; o = align256(o + 2 * sizeof(float) * (size_t)B * cfg.D * (cfg.D / 2 + 1));
+  L.fftwork = o; o = align256(o + fft_work);
+  L.total = o;
+  return L;
+}
+
+template <class T>
+inline T* ws_ptr(void* ws, size_t off) { return reinterpret_cast<T*>(static_cast<char*>(ws) + off); }
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
+               "f"(d)
+               : "memory");
+}
+
+__device__ __forceinline__ void red_add_v2(float* p, float a, float b) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Host-side launchers (one per translation unit).
+cudaError_t launch_activate(const float* theta, int N, float* gauss, int* status, cudaStream_t s);
+cudaError_t launch_project(const gs_config& cfg, const float* gauss, int N, const float* W, int B,
+                           gs_record* proj, float* gacc, int* status, cudaStream_t s);
+cudaError_t launch_bin(const gs_config& cfg, const WsLayout& L, const gs_record* proj, int B, int N,
+                       void* ws, uint32_t* pair_gauss, size_t cap, uint32_t* ranges,
+                       uint32_t* n_pairs, cudaStream_t s);
+cudaError_t launch_render_fwd(const gs_config& cfg, const gs_record* proj, int N,
+                              const uint32_t* pair_gauss, const uint32_t* ranges, int B, float* Q,
+                              cudaStream_t s);
+cudaError_t launch_render_bwd(const gs_config& cfg, const gs_record* proj, int N,
+                              const uint32_t* pair_gauss, const uint32_t* ranges, int B,
+                              const float* dLdQ, float* gacc, cudaStream_t s);
+cudaError_t launch_bwd_finalize(const gs_config& cfg, const float* theta, const float* gauss, int N,
+                                const float* W, int B, float* gacc, float* dtheta, cudaStream_t s);
+cudaError_t launch_ctf_mul(const gs_config& cfg, float2* spec, const float* ctf, int B, cudaStream_t s);
+cudaError_t launch_loss(const gs_config& cfg, const float* X, const float* Y, int B, float* loss,
+                        float* dLdX, cudaStream_t s);
+cudaError_t launch_adam(float* theta, const float* g, float* m, float* v, int n, float lr,
+                        float b1, float b2, float eps, float c1, float c2, cudaStream_t s);
+
+}  // namespace gs

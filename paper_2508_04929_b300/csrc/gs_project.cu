@@ -1,0 +1,177 @@
+// BuildGaussians, ViewingTransform and Projection (Algorithm 2; Sec. 3.3.1-3.3.3, Eqs. 5, 6,
+// 8; App. A.2 Eqs. 12-13).
+//
+// k_activate runs once per Gaussian (pose independent): softplus of the scales and the
+// amplitude, quaternion normalization, R(q) and M = R diag(s).  k_project runs once per
+// (particle, Gaussian): mu_dot = W mu, Sigma_tilde = (W M)_{2x3} (W M)_{2x3}^T, the k-sigma
+// support box, and the record consumed by the rasterizer.
+//
+// The support box is an integer decision.  It is computed with explicitly rounded FP32
+// intrinsics (no FMA contraction) in a fixed order, so that any FP32 implementation of the
+// same sequence reproduces it bit for bit (the order is spelled out in include/gs.h).  The
+// four activations are evaluated in FP64 and rounded once, so that they are the correctly
+// rounded FP32 values with overwhelming probability.
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+__device__ __forceinline__ double softplus_d(double x) {
+  return fmax(x, 0.0) + log1p(exp(-fabs(x)));
+}
+
+__global__ void k_activate(const float* __restrict__ theta, int N, float* __restrict__ gauss,
+                           int* __restrict__ status) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= N) return;
+  const float* t = theta + (size_t)g * 11;
+  float th[11];
+#pragma unroll
+  for (int k = 0; k < 11; ++k) th[k] = t[k];
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < 11; ++k) bad |= !isfinite(th[k]);
+
+  float s0 = (float)softplus_d((double)th[3]);
+  float s1 = (float)softplus_d((double)th[4]);
+  float s2 = (float)softplus_d((double)th[5]);
+  float A = (float)softplus_d((double)th[10]);
+
+  float qw = th[6], qx = th[7], qy = th[8], qz = th[9];
+  float n2 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(qw, qw), __fmul_rn(qx, qx)), __fmul_rn(qy, qy)),
+                       __fmul_rn(qz, qz));
+  float nr = __fsqrt_rn(n2);
+  float w = __fdiv_rn(qw, nr), x = __fdiv_rn(qx, nr), y = __fdiv_rn(qy, nr), z = __fdiv_rn(qz, nr);
+  float xx = __fmul_rn(x, x), yy = __fmul_rn(y, y), zz = __fmul_rn(z, z);
+  float xy = __fmul_rn(x, y), xz = __fmul_rn(x, z), yz = __fmul_rn(y, z);
+  float wx = __fmul_rn(w, x), wy = __fmul_rn(w, y), wz = __fmul_rn(w, z);
+  float R[9];
+  R[0] = __fsub_rn(1.f, __fmul_rn(2.f, __fadd_rn(yy, zz)));
+  R[1] = __fmul_rn(2.f, __fsub_rn(xy, wz));
+  R[2] = __fmul_rn(2.f, __fadd_rn(xz, wy));
+  R[3] = __fmul_rn(2.f, __fadd_rn(xy, wz));
+  R[4] = __fsub_rn(1.f, __fmul_rn(2.f, __fadd_rn(xx, zz)));
+  R[5] = __fmul_rn(2.f, __fsub_rn(yz, wx));
+  R[6] = __fmul_rn(2.f, __fsub_rn(xz, wy));
+  R[7] = __fmul_rn(2.f, __fadd_rn(yz, wx));
+  R[8] = __fsub_rn(1.f, __fmul_rn(2.f, __fadd_rn(xx, yy)));
+  float s[3] = {s0, s1, s2};
+  float* o = gauss + (size_t)g * kGaussStride;
+  o[kMu + 0] = th[0];
+  o[kMu + 1] = th[1];
+  o[kMu + 2] = th[2];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int m = 0; m < 3; ++m) o[kM + 3 * k + m] = __fmul_rn(R[3 * k + m], s[m]);
+  o[kS + 0] = s0;
+  o[kS + 1] = s1;
+  o[kS + 2] = s2;
+  o[kA] = A;
+  o[kSprod] = s0 * s1 * s2;
+  bad |= !isfinite(nr) || nr == 0.f;
+  o[kBad] = bad ? 1.f : 0.f;
+  o[18] = 0.f;
+  o[19] = 0.f;
+  if (bad) atomicOr(status, GS_STATUS_NONFINITE);
+}
+
+__global__ void k_project(const float* __restrict__ gauss, int N, const float* __restrict__ Wall, int D,
+                          float E, float kcut, gs_record* __restrict__ proj, float* __restrict__ gacc,
+                          int* __restrict__ status) {
+  const int b = blockIdx.y;
+  __shared__ float Ws[9];
+  if (threadIdx.x < 9) Ws[threadIdx.x] = Wall[(size_t)b * 9 + threadIdx.x];
+  __syncthreads();
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= N) return;
+  const float* G = gauss + (size_t)g * kGaussStride;
+  float mux = G[kMu], muy = G[kMu + 1], muz = G[kMu + 2];
+  float M[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) M[k] = G[kM + k];
+  bool bad = G[kBad] != 0.f;
+
+  // V = W_{2x3} M, Sigma_tilde = V V^T (Eqs. 5, 6, 12)
+  float V[2][3];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+      V[a][m] = __fadd_rn(__fadd_rn(__fmul_rn(Ws[3 * a + 0], M[0 + m]), __fmul_rn(Ws[3 * a + 1], M[3 + m])),
+                          __fmul_rn(Ws[3 * a + 2], M[6 + m]));
+  float Sxx = __fadd_rn(__fadd_rn(__fmul_rn(V[0][0], V[0][0]), __fmul_rn(V[0][1], V[0][1])),
+                        __fmul_rn(V[0][2], V[0][2]));
+  float Syy = __fadd_rn(__fadd_rn(__fmul_rn(V[1][0], V[1][0]), __fmul_rn(V[1][1], V[1][1])),
+                        __fmul_rn(V[1][2], V[1][2]));
+  float mx = __fadd_rn(__fadd_rn(__fmul_rn(Ws[0], mux), __fmul_rn(Ws[1], muy)), __fmul_rn(Ws[2], muz));
+  float my = __fadd_rn(__fadd_rn(__fmul_rn(Ws[3], mux), __fmul_rn(Ws[4], muy)), __fmul_rn(Ws[5], muz));
+  float inv_h = __fdiv_rn((float)D, __fmul_rn(2.f, E));
+  float c0 = (float)(D / 2);
+  float cx = __fadd_rn(__fmul_rn(mx, inv_h), c0);
+  float cy = __fsub_rn(c0, __fmul_rn(my, inv_h));
+  float rx = __fmul_rn(kcut, __fmul_rn(__fsqrt_rn(Sxx), inv_h));
+  float ry = __fmul_rn(kcut, __fmul_rn(__fsqrt_rn(Syy), inv_h));
+  bad |= !(isfinite(cx) && isfinite(cy) && isfinite(rx) && isfinite(ry));
+
+  // Value path (free FP32).  det Sigma_tilde by the Schur-complement identity
+  // det(Sigma_tilde) = det(Sigma) * (w_z^T Sigma^-1 w_z), w_z the third row of W:
+  // sqrt(det) = s0 s1 s2 * || (w_z^T M)_m / s_m^2 ||, a sum of squares (no cancellation).
+  float Sxy = V[0][0] * V[1][0] + V[0][1] * V[1][1] + V[0][2] * V[1][2];
+  float s0 = G[kS], s1 = G[kS + 1], s2 = G[kS + 2];
+  float t0 = (Ws[6] * M[0] + Ws[7] * M[3] + Ws[8] * M[6]) / (s0 * s0);
+  float t1 = (Ws[6] * M[1] + Ws[7] * M[4] + Ws[8] * M[7]) / (s1 * s1);
+  float t2 = (Ws[6] * M[2] + Ws[7] * M[5] + Ws[8] * M[8]) / (s2 * s2);
+  float sqrt_det = G[kSprod] * sqrtf(t0 * t0 + t1 * t1 + t2 * t2);
+  float det = sqrt_det * sqrt_det;
+  float wgt = G[kA] * kInv2Pi / sqrt_det;
+  float k2 = -0.5f * kLog2e / (det * inv_h * inv_h);
+  bad |= !(isfinite(wgt) && isfinite(k2) && sqrt_det > 0.f);
+
+  gs_record r;
+  r.cx = cx;
+  r.cy = cy;
+  r.ca = k2 * Syy;
+  r.cb = 2.f * k2 * Sxy;
+  r.cc = k2 * Sxx;
+  r.w = wgt;
+  r.x0 = 1; r.x1 = 0; r.y0 = 1; r.y1 = 0;
+  if (!bad) {
+    float x0f = fmaxf(ceilf(__fsub_rn(cx, rx)), 0.f);
+    float x1f = fminf(floorf(__fadd_rn(cx, rx)), (float)(D - 1));
+    float y0f = fmaxf(ceilf(__fsub_rn(cy, ry)), 0.f);
+    float y1f = fminf(floorf(__fadd_rn(cy, ry)), (float)(D - 1));
+    if (x0f <= x1f && y0f <= y1f) {
+      r.x0 = (int16_t)x0f; r.x1 = (int16_t)x1f; r.y0 = (int16_t)y0f; r.y1 = (int16_t)y1f;
+    }
+  } else {
+    atomicOr(status, GS_STATUS_NONFINITE);
+  }
+  size_t idx = (size_t)b * N + g;
+  float4* dst = reinterpret_cast<float4*>(proj + idx);
+  const float4* srcp = reinterpret_cast<const float4*>(&r);
+  dst[0] = srcp[0];
+  dst[1] = srcp[1];
+  // reset this pair's gradient partials for the next gs_render_bwd
+  float4* ga = reinterpret_cast<float4*>(gacc + idx * kGradStride);
+  ga[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+  ga[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+}  // namespace
+
+cudaError_t launch_activate(const float* theta, int N, float* gauss, int* status, cudaStream_t s) {
+  if (N <= 0) return cudaSuccess;
+  k_activate<<<(N + 255) / 256, 256, 0, s>>>(theta, N, gauss, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project(const gs_config& cfg, const float* gauss, int N, const float* W, int B,
+                           gs_record* proj, float* gacc, int* status, cudaStream_t s) {
+  if (N <= 0 || B <= 0) return cudaSuccess;
+  dim3 grid((N + 255) / 256, B);
+  k_project<<<grid, 256, 0, s>>>(gauss, N, W, cfg.D, cfg.E, cfg.cutoff_sigma, proj, gacc, status);
+  return cudaGetLastError();
+}
+
+}  // namespace gs

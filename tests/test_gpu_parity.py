@@ -1,0 +1,298 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle.
+
+Tolerances: images (Q, X) relative L2 <= 1e-5 per image; gradients relative L2 <= 1e-3
+per parameter group (mu, s, q, A) over all Gaussians; integer work (support boxes, tile
+pairs, ranges) bit-exact.  Inputs are seeded synthetic batches shaped like the paper's
+workloads (paper_2508_04929_b300.synth).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2508_04929_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2508_04929_b300 import build  # noqa: E402
+
+build.build()
+from paper_2508_04929_b300 import _lib as L  # noqa: E402
+from paper_2508_04929_b300.splat import Splatter  # noqa: E402
+
+DEV = "cuda"
+GROUPS = (("mu", slice(0, 3)), ("s", slice(3, 6)), ("q", slice(6, 10)), ("A", slice(10, 11)))
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def make_batch(seed, D, N, B, snr=0.1, chains=False):
+    rng = synth.rng_for(seed)
+    th = (synth.chain_gaussians if chains else synth.random_gaussians)(N, D, rng)
+    Ws = synth.random_poses(B, rng)
+    ctf = synth.random_ctf(B, rng)
+    ref = synth.random_gaussians(N, D, rng)
+    clean = []
+    for b in range(B):
+        H = O.ctf_image(D, *[float(v) for v in ctf[b, 0:4]], apix=float(ctf[b, 4]))
+        clean.append(O.apply_ctf(O.render_one(ref, Ws[b], D), H))
+    Y = synth.add_noise(np.stack(clean), snr, rng)
+    return th, Ws, ctf, Y
+
+
+def to_dev(*arrs):
+    return [torch.from_numpy(np.ascontiguousarray(a)).to(DEV) for a in arrs]
+
+
+def records(sp):
+    raw = sp.proj[: sp.B * sp.N * 32].view(torch.float32).view(sp.B, sp.N, 8).cpu()
+    f = raw.numpy()
+    box = raw.view(torch.int16).view(sp.B, sp.N, 16)[:, :, 12:16].numpy().astype(np.int64)
+    return f, box
+
+
+def cuda_step(th, Ws, ctf, Y, D, tile=16, chunk=128, reduction=0):
+    N, B = th.shape[0], Ws.shape[0]
+    sp = Splatter(D, N, B, tile=tile, chunk=chunk, reduction=reduction)
+    t, W, c, y = to_dev(th, Ws.reshape(B, 9), ctf, Y)
+    dth = torch.zeros_like(t)
+    loss = sp.forward_backward(t, W, c, y, dth)
+    torch.cuda.synchronize()
+    out = dict(Q=sp.Q.cpu().numpy(), X=sp.X.cpu().numpy(), L=loss.cpu().numpy(), dX=sp.dX.cpu().numpy(),
+               dQ=sp.dQ.cpu().numpy(), dtheta=dth.cpu().numpy(), status=sp.status(),
+               n_pairs=int(sp.n_pairs.item()) & 0xFFFFFFFF,
+               pairs=sp.pairs.cpu().numpy().view(np.uint32), ranges=sp.ranges.cpu().numpy().view(np.uint32))
+    out["rec"], out["box"] = records(sp)
+    sp.close()
+    return out
+
+
+@pytest.fixture(scope="module")
+def c1():
+    """Config 1: D = 64, N = 2000, B = 8, SNR 0.1, seed 0."""
+    th, Ws, ctf, Y = make_batch(0, 64, 2000, 8)
+    ref = O.forward_backward(th, Ws, 64, Y, ctf)
+    return th, Ws, ctf, Y, ref
+
+
+def test_support_boxes_and_centres_bit_exact(c1):
+    th, Ws, ctf, Y, _ = c1
+    out = cuda_step(th, Ws, ctf, Y, 64)
+    for b in range(Ws.shape[0]):
+        x0, x1, y0, y1, bad, cx, cy = O.support_fp32(th, Ws[b], 64, centres=True)
+        empty = (x0 > x1) | (y0 > y1)
+        box = out["box"][b]
+        gpu_empty = box[:, 0] > box[:, 1]
+        assert np.array_equal(empty, gpu_empty)
+        ok = ~empty
+        assert np.array_equal(box[ok], np.stack([x0, x1, y0, y1], 1)[ok])
+        assert np.array_equal(out["rec"][b, :, 0], cx) and np.array_equal(out["rec"][b, :, 1], cy)
+    assert out["status"] == 0
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_tile_pairs_bit_exact(c1, tile):
+    th, Ws, ctf, Y, _ = c1
+    out = cuda_step(th, Ws, ctf, Y, 64, tile=tile)
+    pg, ranges = O.tile_pairs(th, Ws, 64, tile)
+    assert out["n_pairs"] == len(pg)
+    assert np.array_equal(out["pairs"][: len(pg)], pg)
+    assert np.array_equal(out["ranges"].reshape(ranges.shape), ranges)
+
+
+def test_forward_images_match_oracle(c1):
+    th, Ws, ctf, Y, ref = c1
+    out = cuda_step(th, Ws, ctf, Y, 64)
+    for b in range(Ws.shape[0]):
+        assert rel_l2(out["Q"][b], ref["Q"][b]) < 1e-5
+        assert rel_l2(out["X"][b], ref["X"][b]) < 1e-5
+    assert np.allclose(out["L"], ref["L"], rtol=1e-5)
+    assert rel_l2(out["dX"], ref["dLdX"]) < 1e-5
+    assert rel_l2(out["dQ"], ref["dLdQ"]) < 1e-5
+
+
+def test_gradients_match_oracle(c1):
+    th, Ws, ctf, Y, ref = c1
+    out = cuda_step(th, Ws, ctf, Y, 64)
+    for name, sl in GROUPS:
+        assert rel_l2(out["dtheta"][:, sl], ref["dtheta"][:, sl]) < 1e-3, name
+
+
+def test_results_do_not_depend_on_tile_or_chunk(c1):
+    """The support rule is tile independent and every pixel sums its Gaussians in index
+    order, so Q is bitwise identical for every tile size and chunk depth."""
+    th, Ws, ctf, Y, _ = c1
+    base = cuda_step(th, Ws, ctf, Y, 64, tile=16, chunk=128)
+    for tile, chunk in ((8, 32), (8, 512), (16, 32), (32, 64), (32, 512)):
+        o = cuda_step(th, Ws, ctf, Y, 64, tile=tile, chunk=chunk)
+        assert np.array_equal(o["Q"], base["Q"]), (tile, chunk)
+        for name, sl in GROUPS:
+            assert rel_l2(o["dtheta"][:, sl], base["dtheta"][:, sl]) < 1e-5
+
+
+@pytest.mark.parametrize("D,tile", [(40, 16), (33, 8), (50, 32)])
+def test_ragged_and_odd_boxes(D, tile):
+    th, Ws, ctf, Y = make_batch(3, D, 300, 3)
+    ref = O.forward_backward(th, Ws, D, Y, ctf)
+    out = cuda_step(th, Ws, ctf, Y, D, tile=tile)
+    pg, ranges = O.tile_pairs(th, Ws, D, tile)
+    assert np.array_equal(out["pairs"][: len(pg)], pg)
+    assert np.array_equal(out["ranges"].reshape(ranges.shape), ranges)
+    for b in range(3):
+        assert rel_l2(out["Q"][b], ref["Q"][b]) < 1e-5
+        assert rel_l2(out["X"][b], ref["X"][b]) < 1e-5
+    for name, sl in GROUPS:
+        assert rel_l2(out["dtheta"][:, sl], ref["dtheta"][:, sl]) < 1e-3, name
+
+
+def test_mean_reduction(c1):
+    th, Ws, ctf, Y, _ = c1
+    ref = O.forward_backward(th, Ws, 64, Y, ctf, reduction=1)
+    out = cuda_step(th, Ws, ctf, Y, 64, reduction=1)
+    assert np.allclose(out["L"], ref["L"], rtol=1e-5)
+    for name, sl in GROUPS:
+        assert rel_l2(out["dtheta"][:, sl], ref["dtheta"][:, sl]) < 1e-3, name
+
+
+def test_adam_step_matches_oracle():
+    rng = synth.rng_for(5)
+    th = rng.standard_normal(11 * 500).astype(np.float32)
+    t, = to_dev(th)
+    m = torch.zeros_like(t)
+    v = torch.zeros_like(t)
+    x, mo, vo = th.astype(np.float64), np.zeros(th.size), np.zeros(th.size)
+    for step in range(1, 6):
+        g = rng.standard_normal(th.size).astype(np.float32)
+        gd, = to_dev(g)
+        L.gs_step(t, gd, m, v, step)
+        x, mo, vo = O.adam_step(x, g, mo, vo, step)
+    assert np.max(np.abs(t.cpu().numpy() - x)) < 1e-6
+
+
+# ---------------------------------------------------------------------------------------
+# Edge cases
+# ---------------------------------------------------------------------------------------
+def test_no_gaussians_gives_zero_image():
+    _, Ws, ctf, Y = make_batch(6, 32, 10, 2)
+    th = np.zeros((0, 11), np.float32)
+    out = cuda_step(th, Ws, ctf, Y, 32)
+    assert np.all(out["Q"] == 0) and out["n_pairs"] == 0
+    assert np.allclose(out["L"], np.sum(Y.astype(np.float64) ** 2, axis=(1, 2)), rtol=1e-5)
+
+
+def test_gaussians_outside_the_box_are_culled():
+    th, Ws, ctf, Y = make_batch(7, 32, 50, 2)
+    th[:, 0:3] = 5.0  # ten box widths away
+    out = cuda_step(th, Ws, ctf, Y, 32)
+    assert np.all(out["Q"] == 0) and out["n_pairs"] == 0
+    assert np.all(out["dtheta"] == 0)
+
+
+def test_nonfinite_gaussian_is_flagged_and_skipped():
+    th, Ws, ctf, Y = make_batch(8, 48, 200, 2)
+    bad = th.copy()
+    bad[17, 4] = np.nan
+    bad[99, 7] = np.inf
+    out = cuda_step(bad, Ws, ctf, Y, 48)
+    assert out["status"] & L.GS_STATUS_NONFINITE
+    keep = np.ones(200, bool)
+    keep[[17, 99]] = False
+    ref = O.forward_backward(th[keep], Ws, 48, Y, ctf)
+    for b in range(2):
+        assert rel_l2(out["Q"][b], ref["Q"][b]) < 1e-5
+    assert np.all(out["dtheta"][~keep] == 0)
+    for name, sl in GROUPS:
+        assert rel_l2(out["dtheta"][keep][:, sl], ref["dtheta"][:, sl]) < 1e-3
+
+
+def test_large_gaussian_covering_many_tiles():
+    th, Ws, ctf, Y = make_batch(9, 64, 40, 2)
+    th[0, 3:6] = synth.inv_softplus(np.array([12.0, 9.0, 15.0]) / 64)
+    th[0, 0:3] = 0.0
+    ref = O.forward_backward(th, Ws, 64, Y, ctf)
+    out = cuda_step(th, Ws, ctf, Y, 64, tile=8)
+    for b in range(2):
+        assert rel_l2(out["Q"][b], ref["Q"][b]) < 1e-5
+    for name, sl in GROUPS:
+        assert rel_l2(out["dtheta"][:, sl], ref["dtheta"][:, sl]) < 1e-3, name
+
+
+def test_pair_overflow_is_reported_and_recovered(c1):
+    th, Ws, ctf, Y, ref = c1
+    sp = Splatter(64, th.shape[0], Ws.shape[0], tile=16, pair_capacity=100)
+    t, W, c = to_dev(th, Ws.reshape(-1, 9), ctf)
+    sp.project(t, W)
+    sp.bin_sort(grow=False)
+    need = int(sp.n_pairs.item())
+    assert need > 100
+    assert sp.status() & L.GS_STATUS_OVERFLOW
+    r = sp.ranges.cpu().numpy().view(np.uint32)
+    assert r.max() <= 100
+    sp.bin_sort(grow=True)
+    sp.render()
+    assert sp.status() == 0
+    Q = sp.Q.cpu().numpy()
+    for b in range(Ws.shape[0]):
+        assert rel_l2(Q[b], ref["Q"][b]) < 1e-5
+    sp.close()
+
+
+def test_invalid_arguments_raise():
+    cfg = L.config(64)
+    t = torch.zeros(10, 11, device=DEV)
+    W = torch.zeros(2, 9, device=DEV)
+    with pytest.raises(L.GsError):
+        L.gs_project(L.config(64, tile=12), t, W, torch.empty(640, dtype=torch.uint8, device=DEV),
+                     torch.empty(1 << 20, dtype=torch.uint8, device=DEV))
+    small_ws = torch.empty(256, dtype=torch.uint8, device=DEV)
+    with pytest.raises(L.GsError) as e:
+        L.gs_project(cfg, t, W, torch.empty(640, dtype=torch.uint8, device=DEV), small_ws)
+    assert e.value.rc == L.GS_ENOSPC
+
+
+# ---------------------------------------------------------------------------------------
+# Full size, as the bench launches it: sampled images and gradients, all tile counts
+# ---------------------------------------------------------------------------------------
+@pytest.mark.slow
+def test_full_size_sampled_against_oracle():
+    D, N, B, tile = 256, 100_000, 128, 16
+    rng = synth.rng_for(0)
+    th = synth.random_gaussians(N, D, rng)
+    Ws = synth.random_poses(B, rng)
+    ctf = synth.random_ctf(B, rng)
+    sp = Splatter(D, N, B, tile=tile)
+    t, W, c = to_dev(th, Ws.reshape(B, 9), ctf)
+    sp.forward(t, W, c)
+    torch.cuda.synchronize()
+    counts = O.tile_counts(th, Ws, D, tile)
+    r = sp.ranges.cpu().numpy().view(np.uint32).reshape(B, -1, 2).astype(np.int64)
+    assert np.array_equal(r[:, :, 1] - r[:, :, 0], counts)
+    assert int(sp.n_pairs.item()) == counts.sum()
+    pairs = sp.pairs.cpu().numpy().view(np.uint32)
+    Q = sp.Q.cpu().numpy()
+    for b in (0, 127):
+        x0, x1, y0, y1, _ = O.support_fp32(th, Ws[b], D)
+        for tt in (0, 100, 137, 255):
+            ty, tx = divmod(tt, D // tile)
+            hit = (x0 <= x1) & (y0 <= y1) & (x0 // tile <= tx) & (x1 // tile >= tx) & (y0 // tile <= ty) & (y1 // tile >= ty)
+            assert np.array_equal(pairs[r[b, tt, 0]:r[b, tt, 1]], np.nonzero(hit)[0])
+        assert rel_l2(Q[b], O.render_one(th, Ws[b], D)) < 1e-5
+    # gradient of one image inside the full batch launch
+    dQ = np.zeros((B, D, D), np.float32)
+    dQ[5] = synth.smooth_field(1, D, rng, scale=1e-3)[0]
+    dq, = to_dev(dQ)
+    dth = torch.zeros_like(t)
+    sp.backward(t, W, dq, dth)
+    g = dth.cpu().numpy()
+    ref = O.backward(th, Ws[5:6], D, dQ[5:6])
+    for name, sl in GROUPS:
+        assert rel_l2(g[:, sl], ref[:, sl]) < 1e-3, name
+    assert sp.status() == 0
+    sp.close()
