@@ -189,6 +189,30 @@ int gs_render_bwd(const gs_config* cfg, const float* theta, int N, const float* 
 int gs_step(float* theta, const float* dtheta, float* m, float* v, int n, int t, float lr,
             float beta1, float beta2, float eps, gs_stream_t stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Binning without a caller workspace
+ * ------------------------------------------------------------------------------------- */
+
+/* gs_bin_sort_noalloc: the same binning and sort as gs_bin_sort, with the same outputs,
+ * for callers that cannot allocate device memory -- e.g. a plug-in inside a host
+ * application that manages every byte of device memory through its own pool and forbids
+ * other allocations, or a pipeline that must not allocate while running because
+ * cudaMalloc can synchronize the device.  The paper has no counterpart to this entry
+ * point; it exists only for such callers.
+ * The scratch space is a file-scope device array of 8 MiB that every GPU loading the
+ * library holds until the process exits; this call allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library routine).  The scratch needed for (cfg, B, N) is written
+ * to *scratch_needed (host, may be NULL); if it exceeds 8 MiB the call returns GS_ENOSPC
+ * and does nothing else.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it: make that first call
+ * before capturing any stream.  All calls on a device share the array and leave their
+ * contents in it (the call clears what must start at zero); calls whose GPU work
+ * overlaps -- on different streams without ordering -- race on the array.  Overflow of
+ * pair_capacity is visible as *n_pairs > pair_capacity (the status word is internal). */
+int gs_bin_sort_noalloc(const gs_config* cfg, const gs_record* proj, int B, int N,
+                        uint32_t* pair_gauss, size_t pair_capacity, uint32_t* tile_ranges,
+                        uint32_t* n_pairs, gs_stream_t stream, size_t* scratch_needed);
+
 #ifdef __cplusplus
 }
 #endif

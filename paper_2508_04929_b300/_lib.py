@@ -65,6 +65,7 @@ _SIGS = {
     "gs_loss": [_CFG, _P, _P, _I, _P, _P, _P],
     "gs_render_bwd": [_CFG, _P, _I, _P, _I, _P, _P, _P, _P, _P, _P, _S, _P],
     "gs_step": [_P, _P, _P, _P, _I, _I, _F, _F, _F, _F, _P],
+    "gs_bin_sort_noalloc": [_CFG, _P, _I, _I, _P, _S, _P, _P, _P, ctypes.POINTER(_S)],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(lib, _name)
@@ -164,3 +165,14 @@ def gs_render_bwd(cfg, theta, W, proj, pair_gauss, tile_ranges, dLdQ, dtheta, ws
 def gs_step(theta, dtheta, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None) -> None:
     _check("gs_step", lib.gs_step(_ptr(theta), _ptr(dtheta), _ptr(m), _ptr(v), theta.numel(), int(t), float(lr),
                                   float(beta1), float(beta2), float(eps), _stream(stream)))
+
+
+def gs_bin_sort_noalloc(cfg, proj, B, N, pair_gauss, tile_ranges, n_pairs, stream=None) -> int:
+    """Binning and sort with the library's own fixed device scratch (no workspace, no
+    allocation).  Returns the scratch bytes this size needs."""
+    cap = 0 if pair_gauss is None else pair_gauss.numel()
+    need = _S()
+    _check("gs_bin_sort_noalloc", lib.gs_bin_sort_noalloc(ctypes.byref(cfg), _ptr(proj), B, N, _ptr(pair_gauss), cap,
+                                                          _ptr(tile_ranges), _ptr(n_pairs), _stream(stream),
+                                                          ctypes.byref(need)))
+    return need.value
