@@ -111,8 +111,8 @@ int gs_project(const gs_config* cfg, const float* theta, int N, const float* W, 
   cudaStream_t s = (cudaStream_t)stream;
   float* gauss = ws_ptr<float>(ws, L.gauss);
   int* status = ws_ptr<int>(ws, L.status);
-  cudaError_t e = launch_activate(theta, N, gauss, status, s);
-  if (e == cudaSuccess) e = launch_project(*cfg, gauss, N, W, B, proj, ws_ptr<float>(ws, L.gacc), status, s);
+  cudaError_t e = launch_activate(theta, N, gauss, ws_ptr<float>(ws, L.gacc), status, s);
+  if (e == cudaSuccess) e = launch_project(*cfg, gauss, N, W, B, proj, status, s);
   return cuda_rc(e);
 }
 
@@ -183,8 +183,8 @@ int gs_render_bwd(const gs_config* cfg, const float* theta, int N, const float* 
   if (ws_bytes < L.spec) return GS_ENOSPC;
   cudaStream_t s = (cudaStream_t)stream;
   float* gacc = ws_ptr<float>(ws, L.gacc);
-  cudaError_t e = launch_render_bwd(*cfg, proj, N, pair_gauss, tile_ranges, B, dLdQ, gacc, s);
-  if (e == cudaSuccess) e = launch_bwd_finalize(*cfg, theta, ws_ptr<float>(ws, L.gauss), N, W, B, gacc, dtheta, s);
+  cudaError_t e = launch_render_bwd(*cfg, proj, N, pair_gauss, tile_ranges, B, dLdQ, W, gacc, s);
+  if (e == cudaSuccess) e = launch_bwd_finalize(theta, ws_ptr<float>(ws, L.gauss), N, gacc, dtheta, s);
   return cuda_rc(e);
 }
 

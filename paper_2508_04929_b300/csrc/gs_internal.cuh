@@ -11,7 +11,7 @@ namespace gs {
 constexpr int kBinChunk = 2048;       // Gaussians per binning CTA (8 warps x 256, in order)
 constexpr int kBinWarps = 8;
 constexpr int kGaussStride = 20;      // floats per activated Gaussian in the workspace
-constexpr int kGradStride = 8;        // floats per (particle, Gaussian) gradient partial
+constexpr int kGradStride = 12;       // floats per Gaussian in the gradient accumulator
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kInv2Pi = 0.15915494309189535f;
 
@@ -47,7 +47,7 @@ inline WsLayout ws_layout(const gs_config& cfg, int B, int N, size_t fft_work) {
   L.ttotal = o; o = align256(o + sizeof(uint32_t) * (size_t)B * L.Tn);
   L.itotal = o; o = align256(o + sizeof(uint32_t) * ((size_t)B + 1));
   L.ibase = o; o = align256(o + sizeof(unsigned long long) * ((size_t)B + 1));
-  L.gacc = o; o = align256(o + sizeof(float) * kGradStride * (size_t)B * N);
+  L.gacc = o; o = align256(o + sizeof(float) * kGradStride * (size_t)N);
   L.spec = o; o = align256(o + 2 * sizeof(float) * (size_t)B * cfg.D * (cfg.D / 2 + 1));
   L.fftwork = o; o = align256(o + fft_work);
   L.total = o;
@@ -80,9 +80,9 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 
 // Host-side launchers (one per translation unit).
-cudaError_t launch_activate(const float* theta, int N, float* gauss, int* status, cudaStream_t s);
+cudaError_t launch_activate(const float* theta, int N, float* gauss, float* gacc, int* status, cudaStream_t s);
 cudaError_t launch_project(const gs_config& cfg, const float* gauss, int N, const float* W, int B,
-                           gs_record* proj, float* gacc, int* status, cudaStream_t s);
+                           gs_record* proj, int* status, cudaStream_t s);
 cudaError_t launch_bin(const gs_config& cfg, const WsLayout& L, const gs_record* proj, int B, int N,
                        void* ws, uint32_t* pair_gauss, size_t cap, uint32_t* ranges,
                        uint32_t* n_pairs, cudaStream_t s);
@@ -91,9 +91,9 @@ cudaError_t launch_render_fwd(const gs_config& cfg, const gs_record* proj, int N
                               cudaStream_t s);
 cudaError_t launch_render_bwd(const gs_config& cfg, const gs_record* proj, int N,
                               const uint32_t* pair_gauss, const uint32_t* ranges, int B,
-                              const float* dLdQ, float* gacc, cudaStream_t s);
-cudaError_t launch_bwd_finalize(const gs_config& cfg, const float* theta, const float* gauss, int N,
-                                const float* W, int B, float* gacc, float* dtheta, cudaStream_t s);
+                              const float* dLdQ, const float* W, float* gacc, cudaStream_t s);
+cudaError_t launch_bwd_finalize(const float* theta, const float* gauss, int N, float* gacc, float* dtheta,
+                                cudaStream_t s);
 cudaError_t launch_ctf_mul(const gs_config& cfg, float2* spec, const float* ctf, int B, cudaStream_t s);
 cudaError_t launch_loss(const gs_config& cfg, const float* X, const float* Y, int B, float* loss,
                         float* dLdX, cudaStream_t s);

@@ -21,7 +21,7 @@ __device__ __forceinline__ double softplus_d(double x) {
 }
 
 __global__ void k_activate(const float* __restrict__ theta, int N, float* __restrict__ gauss,
-                           int* __restrict__ status) {
+                           float* __restrict__ gacc, int* __restrict__ status) {
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= N) return;
   const float* t = theta + (size_t)g * 11;
@@ -73,12 +73,16 @@ __global__ void k_activate(const float* __restrict__ theta, int N, float* __rest
   o[kBad] = bad ? 1.f : 0.f;
   o[18] = 0.f;
   o[19] = 0.f;
+  // reset this Gaussian's gradient accumulator for the next gs_render_bwd
+  float4* ga = reinterpret_cast<float4*>(gacc + (size_t)g * kGradStride);
+  ga[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+  ga[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+  ga[2] = make_float4(0.f, 0.f, 0.f, 0.f);
   if (bad) atomicOr(status, GS_STATUS_NONFINITE);
 }
 
 __global__ void k_project(const float* __restrict__ gauss, int N, const float* __restrict__ Wall, int D,
-                          float E, float kcut, gs_record* __restrict__ proj, float* __restrict__ gacc,
-                          int* __restrict__ status) {
+                          float E, float kcut, gs_record* __restrict__ proj, int* __restrict__ status) {
   const int b = blockIdx.y;
   __shared__ float Ws[9];
   if (threadIdx.x < 9) Ws[threadIdx.x] = Wall[(size_t)b * 9 + threadIdx.x];
@@ -152,25 +156,21 @@ __global__ void k_project(const float* __restrict__ gauss, int N, const float* _
   const float4* srcp = reinterpret_cast<const float4*>(&r);
   dst[0] = srcp[0];
   dst[1] = srcp[1];
-  // reset this pair's gradient partials for the next gs_render_bwd
-  float4* ga = reinterpret_cast<float4*>(gacc + idx * kGradStride);
-  ga[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-  ga[1] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 }  // namespace
 
-cudaError_t launch_activate(const float* theta, int N, float* gauss, int* status, cudaStream_t s) {
+cudaError_t launch_activate(const float* theta, int N, float* gauss, float* gacc, int* status, cudaStream_t s) {
   if (N <= 0) return cudaSuccess;
-  k_activate<<<(N + 255) / 256, 256, 0, s>>>(theta, N, gauss, status);
+  k_activate<<<(N + 255) / 256, 256, 0, s>>>(theta, N, gauss, gacc, status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_project(const gs_config& cfg, const float* gauss, int N, const float* W, int B,
-                           gs_record* proj, float* gacc, int* status, cudaStream_t s) {
+                           gs_record* proj, int* status, cudaStream_t s) {
   if (N <= 0 || B <= 0) return cudaSuccess;
   dim3 grid((N + 255) / 256, B);
-  k_project<<<grid, 256, 0, s>>>(gauss, N, W, cfg.D, cfg.E, cfg.cutoff_sigma, proj, gacc, status);
+  k_project<<<grid, 256, 0, s>>>(gauss, N, W, cfg.D, cfg.E, cfg.cutoff_sigma, proj, status);
   return cudaGetLastError();
 }
 
