@@ -1,0 +1,123 @@
+"""torch.autograd wrappers of the splatting path (render, CTF, loss).
+
+``render(theta, W, engine)`` returns Q[B, D, D] and differentiates to theta through the
+hand-written backward (gs_render_bwd).  The engine processes the particles in chunks and,
+in the backward pass, recomputes each chunk's projection and per-tile Gaussian lists
+(gs_project + gs_bin_sort) instead of keeping them alive between forward and backward, so
+the memory held across the two passes is theta, W and Q only, whatever the batch size.
+``apply_ctf`` (self-adjoint, so its backward is itself) and ``loss`` complete the image
+formation model X = F^-1(H F Q), L = ||X - Y||^2 (App. A.2 Eq. 14, Sec. 3.3.5).
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _lib as L
+from .splat import Splatter
+
+
+class RenderEngine:
+    """Chunked render / backward with recomputed tile lists."""
+
+    def __init__(self, D, N, particles_per_chunk=64, tile=16, chunk=128, E=0.5, cutoff_sigma=3.0,
+                 reduction=0, device="cuda"):
+        self.D, self.N, self.P = int(D), int(N), int(particles_per_chunk)
+        self.kw = dict(tile=tile, chunk=chunk, E=E, cutoff_sigma=cutoff_sigma, reduction=reduction, device=device)
+        self._sp = {}
+
+    def _splatter(self, B):
+        if B not in self._sp:
+            self._sp[B] = Splatter(self.D, self.N, B, **self.kw)
+        return self._sp[B]
+
+    def _chunks(self, B):
+        for b0 in range(0, B, self.P):
+            yield b0, min(B, b0 + self.P)
+
+    def render(self, theta, W):
+        B = W.shape[0]
+        Q = torch.empty((B, self.D, self.D), dtype=torch.float32, device=theta.device)
+        for b0, b1 in self._chunks(B):
+            sp = self._splatter(b1 - b0)
+            sp.project(theta, W[b0:b1])
+            sp.bin_sort(grow=True)
+            sp.render(out=Q[b0:b1])
+        return Q
+
+    def render_backward(self, theta, W, dQ):
+        dtheta = torch.zeros_like(theta)
+        for b0, b1 in self._chunks(W.shape[0]):
+            sp = self._splatter(b1 - b0)
+            sp.project(theta, W[b0:b1])  # recompute the lists of this chunk
+            sp.bin_sort(grow=True)
+            sp.backward(theta, W[b0:b1], dQ[b0:b1].contiguous(), dtheta)
+        return dtheta
+
+    def apply_ctf(self, inp, ctf):
+        out = torch.empty_like(inp)
+        for b0, b1 in self._chunks(inp.shape[0]):
+            sp = self._splatter(b1 - b0)
+            sp.apply_ctf(inp[b0:b1].contiguous(), ctf[b0:b1].contiguous(), out[b0:b1])
+        return out
+
+    def close(self):
+        for sp in self._sp.values():
+            sp.close()
+        self._sp.clear()
+
+
+class _Render(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, theta, W, engine):
+        ctx.engine = engine
+        ctx.save_for_backward(theta, W)
+        return engine.render(theta.contiguous(), W.contiguous())
+
+    @staticmethod
+    def backward(ctx, dQ):
+        theta, W = ctx.saved_tensors
+        return ctx.engine.render_backward(theta.contiguous(), W.contiguous(), dQ.contiguous()), None, None
+
+
+class _CTF(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, Q, ctf, engine):
+        ctx.engine = engine
+        ctx.save_for_backward(ctf)
+        return engine.apply_ctf(Q.contiguous(), ctf)
+
+    @staticmethod
+    def backward(ctx, dX):
+        (ctf,) = ctx.saved_tensors
+        return ctx.engine.apply_ctf(dX.contiguous(), ctf), None, None  # H_hat real and even
+
+
+class _Loss(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, X, Y, cfg):
+        B = X.shape[0]
+        loss = torch.empty(B, dtype=torch.float32, device=X.device)
+        dX = torch.empty_like(X)
+        L.gs_loss(cfg, X.contiguous(), Y.contiguous(), loss, dX)
+        ctx.save_for_backward(dX)
+        return loss
+
+    @staticmethod
+    def backward(ctx, dloss):
+        (dX,) = ctx.saved_tensors
+        return dX * dloss.view(-1, 1, 1), None, None
+
+
+def render(theta, W, engine: RenderEngine):
+    """Q[B, D, D] = Rasterize(theta, W) (Algorithm 2), differentiable in theta."""
+    return _Render.apply(theta, W, engine)
+
+
+def apply_ctf(Q, ctf, engine: RenderEngine):
+    """X = F^-1(H_hat . F(Q)) per image (App. A.2 Eq. 14), differentiable in Q."""
+    return _CTF.apply(Q, ctf, engine)
+
+
+def loss(X, Y, D, reduction=0):
+    """Per-image L = ||X - Y||^2 (Sec. 3.3.5), differentiable in X."""
+    return _Loss.apply(X, Y, L.config(D, reduction=reduction))

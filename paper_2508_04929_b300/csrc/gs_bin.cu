@@ -15,7 +15,8 @@
 //
 // Inside a warp the rank of lane l's instance in tile (tx, ty) is the number of lower lanes
 // whose box covers that tile: popc(colmask[tx] & rowmask[ty] & lanemask_lt), where
-// colmask[tx] / rowmask[ty] are ballots over the lanes' tile-column / tile-row ranges.
+// colmask[tx] / rowmask[ty] are the lanes whose tile-column / tile-row range holds tx / ty,
+// obtained for all tx at once by a 32 x 32 bit transpose of the lanes' range masks.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -32,6 +33,32 @@ __device__ __forceinline__ bool load_rect(const gs_record* proj, size_t idx, int
   if (x0 > x1 || y0 > y1) return false;
   r.tx0 = x0 / T; r.tx1 = x1 / T; r.ty0 = y0 / T; r.ty1 = y1 / T;
   return true;
+}
+
+// Bits [lo, hi] of the 32-bit word that holds positions [base, base + 32) (0 if disjoint).
+__device__ __forceinline__ unsigned range_bits(int lo, int hi, int base) {
+  lo -= base;
+  hi -= base;
+  if (hi < 0 || lo > 31 || lo > hi) return 0u;
+  lo = max(lo, 0);
+  hi = min(hi, 31);
+  const unsigned up = hi >= 31 ? 0xffffffffu : ((2u << hi) - 1u);
+  return up & ~((1u << lo) - 1u);
+}
+
+// Transpose of the 32 x 32 bit matrix whose row l is lane l's word: on return lane x
+// holds column x (bit l = bit x of lane l's input).
+__device__ __forceinline__ unsigned transpose32(unsigned x) {
+  const int lane = threadIdx.x & 31;
+  const unsigned masks[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int j = 16 >> s;
+    const unsigned m = masks[s];
+    const unsigned o = __shfl_xor_sync(0xffffffffu, x, j);
+    x = (lane & j) ? ((x & ~m) | ((o & ~m) >> j)) : ((x & m) | ((o & m) << j));
+  }
+  return x;
 }
 
 __global__ void k_bin_count(const gs_record* __restrict__ proj, int N, int T, int ntx, int Tn, int C,
@@ -96,17 +123,23 @@ __device__ uint32_t block_exclusive_scan(uint32_t* v, int n) {
   return total;
 }
 
-__global__ void k_bin_scan(uint32_t* __restrict__ hist, int Tn, int C, uint32_t* __restrict__ tstart,
+__global__ void __launch_bounds__(1024) k_bin_scan(uint32_t* __restrict__ hist, int Tn, int C, uint32_t* __restrict__ tstart,
                            uint32_t* __restrict__ ttotal, uint32_t* __restrict__ itotal) {
   extern __shared__ uint32_t sh[];  // Tn
   const int b = blockIdx.x;
   uint32_t* H = hist + (size_t)b * C * Tn;
+  constexpr int kBatch = 8;  // independent loads in flight per thread
   for (int t = threadIdx.x; t < Tn; t += blockDim.x) {
     uint32_t run = 0;
-    for (int c = 0; c < C; ++c) {
-      uint32_t v = H[(size_t)c * Tn + t];
-      H[(size_t)c * Tn + t] = run;
-      run += v;
+    for (int c0 = 0; c0 < C; c0 += kBatch) {
+      uint32_t v[kBatch];
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) v[j] = (c0 + j < C) ? H[(size_t)(c0 + j) * Tn + t] : 0u;
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        if (c0 + j < C) H[(size_t)(c0 + j) * Tn + t] = run;
+        run += v[j];
+      }
     }
     sh[t] = run;
     ttotal[(size_t)b * Tn + t] = run;
@@ -114,9 +147,16 @@ __global__ void k_bin_scan(uint32_t* __restrict__ hist, int Tn, int C, uint32_t*
   __syncthreads();
   uint32_t total = block_exclusive_scan(sh, Tn);
   for (int t = threadIdx.x; t < Tn; t += blockDim.x) {
-    uint32_t st = sh[t];
+    const uint32_t st = sh[t];
     tstart[(size_t)b * Tn + t] = st;
-    for (int c = 0; c < C; ++c) H[(size_t)c * Tn + t] += st;
+    for (int c0 = 0; c0 < C; c0 += kBatch) {
+      uint32_t v[kBatch];
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) v[j] = (c0 + j < C) ? H[(size_t)(c0 + j) * Tn + t] : 0u;
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j)
+        if (c0 + j < C) H[(size_t)(c0 + j) * Tn + t] = v[j] + st;
+    }
   }
   if (threadIdx.x == 0) itotal[b] = total;
 }
@@ -170,45 +210,49 @@ __global__ void k_bin_scatter(const gs_record* __restrict__ proj, int N, int T, 
   __syncthreads();
   // 3. stable scatter, 32 Gaussians per round in lane order
   const unsigned ltmask = lanemask_lt();
+  const bool wide = ntx > 32;
   for (int gr = g0; gr < g1; gr += 32) {
     const int g = gr + lane;
     TileRect r;
     bool valid = (g < g1) && load_rect(proj, (size_t)b * N + g, T, r);
     if (!valid) { r.tx0 = 1; r.tx1 = 0; r.ty0 = 1; r.ty1 = 0; }
-    unsigned colm0 = 0, colm1 = 0, rowm0 = 0, rowm1 = 0;
-    for (int x = 0; x < ntx; ++x) {
-      unsigned mc = __ballot_sync(0xffffffffu, r.tx0 <= x && x <= r.tx1);
-      unsigned mr = __ballot_sync(0xffffffffu, r.ty0 <= x && x <= r.ty1);
-      if ((x & 31) == lane) {
-        if (x < 32) { colm0 = mc; rowm0 = mr; } else { colm1 = mc; rowm1 = mr; }
+    // colmask[x] (in lane x) = lanes whose tile-column range holds x; rowmask likewise
+    const unsigned colm0 = transpose32(range_bits(r.tx0, r.tx1, 0));
+    const unsigned rowm0 = transpose32(range_bits(r.ty0, r.ty1, 0));
+    unsigned colm1 = 0, rowm1 = 0;
+    if (wide) {
+      colm1 = transpose32(range_bits(r.tx0, r.tx1, 32));
+      rowm1 = transpose32(range_bits(r.ty0, r.ty1, 32));
+    }
+    const int cnt = valid ? (r.tx1 - r.tx0 + 1) * (r.ty1 - r.ty0 + 1) : 0;
+    const int kmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)cnt);
+    for (int pass = 0; pass < 2; ++pass) {
+      int cx = r.tx0, cy = r.ty0;
+      for (int k = 0; k < kmax; ++k) {
+        const bool act = k < cnt;
+        const int tx = act ? cx : 0, ty = act ? cy : 0;
+        unsigned cm = __shfl_sync(0xffffffffu, colm0, tx & 31);
+        unsigned rm = __shfl_sync(0xffffffffu, rowm0, ty & 31);
+        if (wide) {
+          const unsigned c1 = __shfl_sync(0xffffffffu, colm1, tx & 31);
+          const unsigned r1 = __shfl_sync(0xffffffffu, rowm1, ty & 31);
+          if (tx >= 32) cm = c1;
+          if (ty >= 32) rm = r1;
+        }
+        const unsigned both = cm & rm;
+        if (act) {
+          const int t = ty * ntx + tx;
+          if (pass == 0) {
+            const unsigned long long pos = base + mycur[t] + __popc(both & ltmask);
+            if (pos < cap) pair_gauss[pos] = (uint32_t)g;
+          } else if ((both >> lane) == 1u) {
+            mycur[t] += __popc(both);  // the highest covering lane moves the cursor
+          }
+        }
+        if (++cx > r.tx1) { cx = r.tx0; ++cy; }
       }
+      __syncwarp();
     }
-    const int wc = valid ? r.tx1 - r.tx0 + 1 : 1;
-    const int cnt = valid ? wc * (r.ty1 - r.ty0 + 1) : 0;
-    int kmax = cnt;
-    for (int o = 16; o > 0; o >>= 1) kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
-    for (int k = 0; k < kmax; ++k) {
-      const bool act = k < cnt;
-      const int tx = act ? r.tx0 + k % wc : 0, ty = act ? r.ty0 + k / wc : 0;
-      unsigned c0 = __shfl_sync(0xffffffffu, colm0, tx & 31), c1 = __shfl_sync(0xffffffffu, colm1, tx & 31);
-      unsigned r0 = __shfl_sync(0xffffffffu, rowm0, ty & 31), r1 = __shfl_sync(0xffffffffu, rowm1, ty & 31);
-      const unsigned both = (tx < 32 ? c0 : c1) & (ty < 32 ? r0 : r1);
-      if (act) {
-        const int t = ty * ntx + tx;
-        unsigned long long pos = base + mycur[t] + __popc(both & ltmask);
-        if (pos < cap) pair_gauss[pos] = (uint32_t)g;
-      }
-    }
-    __syncwarp();
-    for (int k = 0; k < kmax; ++k) {
-      const bool act = k < cnt;
-      const int tx = act ? r.tx0 + k % wc : 0, ty = act ? r.ty0 + k / wc : 0;
-      unsigned c0 = __shfl_sync(0xffffffffu, colm0, tx & 31), c1 = __shfl_sync(0xffffffffu, colm1, tx & 31);
-      unsigned r0 = __shfl_sync(0xffffffffu, rowm0, ty & 31), r1 = __shfl_sync(0xffffffffu, rowm1, ty & 31);
-      const unsigned both = (tx < 32 ? c0 : c1) & (ty < 32 ? r0 : r1);
-      if (act && (both >> lane) == 1u) mycur[ty * ntx + tx] += __popc(both);  // highest covering lane
-    }
-    __syncwarp();
   }
   // 4. tile ranges (absolute, clipped to the pair capacity)
   if (c == 0) {

@@ -3,7 +3,7 @@
 // k_ctf_mul multiplies the R2C half spectrum of each image by H_hat / D^2.  H_hat depends
 // on the integer n = fx^2 + fy^2 only: chi / pi = alpha n - beta n^2 with per-image
 // constants alpha = lambda df / (D apix)^2 and beta = Cs lambda^3 / (2 (D apix)^4), formed
-// once per CTA in FP64.  The phase is reduced modulo 2 exactly (the product alpha_hi * n is
+// once per CTA (a few CTAs per image) in FP64.  The phase is reduced modulo 2 exactly (the product alpha_hi * n is
 // split into its rounded value and its exact FMA remainder), so sinpi / cospi see an
 // argument accurate to ~1e-7 even where chi reaches hundreds of radians.
 #include "gs_internal.cuh"
@@ -32,25 +32,26 @@ __global__ void k_ctf_mul(float2* __restrict__ spec, const float* __restrict__ c
     cst[5] = (float)(1.0 / ((double)D * (double)D));
   }
   __syncthreads();
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= D * W2) return;
-  const int l = idx / W2, m = idx - l * W2;
-  const int fy = l < (D + 1) / 2 ? l : l - D;
-  const float n = (float)(fy * fy + m * m);  // exact (< 2^24)
-  const float p = cst[0] * n;
-  const float perr = fmaf(cst[0], n, -p);  // exact remainder of alpha_hi * n
-  const float pred = p - 2.f * rintf(0.5f * p);  // exact: p mod 2 in [-1, 1]
-  const float q = cst[2] * n * n;
-  const float qred = q - 2.f * rintf(0.5f * q);
-  const float tt = (pred + perr + cst[1] * n) - qred;
-  float sp, cp;
-  sincospif(tt, &sp, &cp);
-  const float H = -(cst[3] * sp + cst[4] * cp) * cst[5];
-  float2* z = spec + (size_t)b * D * W2 + idx;
-  float2 v = *z;
-  v.x *= H;
-  v.y *= H;
-  *z = v;
+  const float a_hi = cst[0], a_lo = cst[1], bet = cst[2], sw = cst[3], wc = cst[4], sc = cst[5];
+  float2* img = spec + (size_t)b * D * W2;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < D * W2; idx += gridDim.x * blockDim.x) {
+    const int l = idx / W2, m = idx - l * W2;
+    const int fy = l < (D + 1) / 2 ? l : l - D;
+    const float n = (float)(fy * fy + m * m);  // exact (< 2^24)
+    const float p = a_hi * n;
+    const float perr = fmaf(a_hi, n, -p);          // exact remainder of alpha_hi * n
+    const float pred = p - 2.f * rintf(0.5f * p);  // exact: p mod 2 in [-1, 1]
+    const float q = bet * n * n;
+    const float qred = q - 2.f * rintf(0.5f * q);
+    const float tt = (pred + perr + a_lo * n) - qred;
+    float sp, cp;
+    sincospif(tt, &sp, &cp);
+    const float H = -(sw * sp + wc * cp) * sc;
+    float2 v = img[idx];
+    v.x *= H;
+    v.y *= H;
+    img[idx] = v;
+  }
 }
 
 __global__ void k_loss(const float* __restrict__ X, const float* __restrict__ Y, int P, float scale,
@@ -92,7 +93,9 @@ __global__ void k_adam(float* __restrict__ th, const float* __restrict__ g, floa
 cudaError_t launch_ctf_mul(const gs_config& cfg, float2* spec, const float* ctf, int B, cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
   const int D = cfg.D, cnt = D * (D / 2 + 1);
-  dim3 grid((cnt + 255) / 256, B);
+  int per_image = (cnt + 255) / 256;
+  if (per_image > 8) per_image = 8;  // a few CTAs per image: few FP64 prologues
+  dim3 grid(per_image, B);
   k_ctf_mul<<<grid, 256, 0, s>>>(spec, ctf, D);
   return cudaGetLastError();
 }

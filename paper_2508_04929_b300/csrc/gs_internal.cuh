@@ -10,7 +10,7 @@ namespace gs {
 
 constexpr int kBinChunk = 2048;       // Gaussians per binning CTA (8 warps x 256, in order)
 constexpr int kBinWarps = 8;
-constexpr int kGaussStride = 20;      // floats per activated Gaussian in the workspace
+constexpr int kGaussStride = 24;      // floats per activated Gaussian in the workspace
 constexpr int kGradStride = 12;       // floats per Gaussian in the gradient accumulator
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kInv2Pi = 0.15915494309189535f;
@@ -23,6 +23,7 @@ enum GaussField {
   kA = 15,     // A
   kSprod = 16, // s0 s1 s2
   kBad = 17,   // 1 if a parameter is not finite
+  kInvS2 = 18, // 1 / s[m]^2
 };
 
 // Workspace carve-up; every part 256-byte aligned.
@@ -83,6 +84,12 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 cudaError_t launch_activate(const float* theta, int N, float* gauss, float* gacc, int* status, cudaStream_t s);
 cudaError_t launch_project(const gs_config& cfg, const float* gauss, int N, const float* W, int B,
                            gs_record* proj, int* status, cudaStream_t s);
+// inv_h = D / (2E) in FP32, correctly rounded (part of the support-box arithmetic)
+inline float inv_pixel(const gs_config& cfg) {
+  volatile float twoE = 2.0f * cfg.E;  // exact
+  volatile float r = (float)cfg.D / twoE;
+  return r;
+}
 cudaError_t launch_bin(const gs_config& cfg, const WsLayout& L, const gs_record* proj, int B, int N,
                        void* ws, uint32_t* pair_gauss, size_t cap, uint32_t* ranges,
                        uint32_t* n_pairs, cudaStream_t s);

@@ -71,8 +71,12 @@ __global__ void k_activate(const float* __restrict__ theta, int N, float* __rest
   o[kSprod] = s0 * s1 * s2;
   bad |= !isfinite(nr) || nr == 0.f;
   o[kBad] = bad ? 1.f : 0.f;
-  o[18] = 0.f;
-  o[19] = 0.f;
+  o[kInvS2 + 0] = 1.f / (s0 * s0);
+  o[kInvS2 + 1] = 1.f / (s1 * s1);
+  o[kInvS2 + 2] = 1.f / (s2 * s2);
+  o[21] = 0.f;
+  o[22] = 0.f;
+  o[23] = 0.f;
   // reset this Gaussian's gradient accumulator for the next gs_render_bwd
   float4* ga = reinterpret_cast<float4*>(gacc + (size_t)g * kGradStride);
   ga[0] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -82,14 +86,22 @@ __global__ void k_activate(const float* __restrict__ theta, int N, float* __rest
 }
 
 __global__ void k_project(const float* __restrict__ gauss, int N, const float* __restrict__ Wall, int D,
-                          float E, float kcut, gs_record* __restrict__ proj, int* __restrict__ status) {
+                          float inv_h, float kcut, gs_record* __restrict__ proj, int* __restrict__ status) {
   const int b = blockIdx.y;
   __shared__ float Ws[9];
   if (threadIdx.x < 9) Ws[threadIdx.x] = Wall[(size_t)b * 9 + threadIdx.x];
   __syncthreads();
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= N) return;
-  const float* G = gauss + (size_t)g * kGaussStride;
+  float G[kGaussStride];
+  {
+    const float4* src = reinterpret_cast<const float4*>(gauss + (size_t)g * kGaussStride);
+#pragma unroll
+    for (int k = 0; k < kGaussStride / 4; ++k) {
+      const float4 v = __ldg(src + k);
+      G[4 * k] = v.x; G[4 * k + 1] = v.y; G[4 * k + 2] = v.z; G[4 * k + 3] = v.w;
+    }
+  }
   float mux = G[kMu], muy = G[kMu + 1], muz = G[kMu + 2];
   float M[9];
 #pragma unroll
@@ -110,7 +122,6 @@ __global__ void k_project(const float* __restrict__ gauss, int N, const float* _
                         __fmul_rn(V[1][2], V[1][2]));
   float mx = __fadd_rn(__fadd_rn(__fmul_rn(Ws[0], mux), __fmul_rn(Ws[1], muy)), __fmul_rn(Ws[2], muz));
   float my = __fadd_rn(__fadd_rn(__fmul_rn(Ws[3], mux), __fmul_rn(Ws[4], muy)), __fmul_rn(Ws[5], muz));
-  float inv_h = __fdiv_rn((float)D, __fmul_rn(2.f, E));
   float c0 = (float)(D / 2);
   float cx = __fadd_rn(__fmul_rn(mx, inv_h), c0);
   float cy = __fsub_rn(c0, __fmul_rn(my, inv_h));
@@ -122,14 +133,13 @@ __global__ void k_project(const float* __restrict__ gauss, int N, const float* _
   // det(Sigma_tilde) = det(Sigma) * (w_z^T Sigma^-1 w_z), w_z the third row of W:
   // sqrt(det) = s0 s1 s2 * || (w_z^T M)_m / s_m^2 ||, a sum of squares (no cancellation).
   float Sxy = V[0][0] * V[1][0] + V[0][1] * V[1][1] + V[0][2] * V[1][2];
-  float s0 = G[kS], s1 = G[kS + 1], s2 = G[kS + 2];
-  float t0 = (Ws[6] * M[0] + Ws[7] * M[3] + Ws[8] * M[6]) / (s0 * s0);
-  float t1 = (Ws[6] * M[1] + Ws[7] * M[4] + Ws[8] * M[7]) / (s1 * s1);
-  float t2 = (Ws[6] * M[2] + Ws[7] * M[5] + Ws[8] * M[8]) / (s2 * s2);
+  float t0 = (Ws[6] * M[0] + Ws[7] * M[3] + Ws[8] * M[6]) * G[kInvS2];
+  float t1 = (Ws[6] * M[1] + Ws[7] * M[4] + Ws[8] * M[7]) * G[kInvS2 + 1];
+  float t2 = (Ws[6] * M[2] + Ws[7] * M[5] + Ws[8] * M[8]) * G[kInvS2 + 2];
   float sqrt_det = G[kSprod] * sqrtf(t0 * t0 + t1 * t1 + t2 * t2);
   float det = sqrt_det * sqrt_det;
-  float wgt = G[kA] * kInv2Pi / sqrt_det;
-  float k2 = -0.5f * kLog2e / (det * inv_h * inv_h);
+  float wgt = __fdividef(G[kA] * kInv2Pi, sqrt_det);
+  float k2 = __fdividef(-0.5f * kLog2e, det * inv_h * inv_h);
   bad |= !(isfinite(wgt) && isfinite(k2) && sqrt_det > 0.f);
 
   gs_record r;
@@ -170,7 +180,7 @@ cudaError_t launch_project(const gs_config& cfg, const float* gauss, int N, cons
                            gs_record* proj, int* status, cudaStream_t s) {
   if (N <= 0 || B <= 0) return cudaSuccess;
   dim3 grid((N + 255) / 256, B);
-  k_project<<<grid, 256, 0, s>>>(gauss, N, W, cfg.D, cfg.E, cfg.cutoff_sigma, proj, status);
+  k_project<<<grid, 256, 0, s>>>(gauss, N, W, cfg.D, inv_pixel(cfg), cfg.cutoff_sigma, proj, status);
   return cudaGetLastError();
 }
 
