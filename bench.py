@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--chunk", type=int, default=0, help="0 = autotune")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--mixed", type=int, default=1, help="also time the mixed-size batch (1/0)")
     p.add_argument("--cpu-sample", type=int, default=0, help="images in the CPU sample (0 = one per core, max 16)")
     return p.parse_args()
 
@@ -159,6 +160,49 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------------------
+# mixed-size batch: 4 volumes (N = 10k/30k/60k/100k at D = 96/128/192/256), 128 particles
+# each, SNR 0.05, one CUDA graph; tile size and chunk depth autotuned per volume
+# ---------------------------------------------------------------------------------------
+MIXED = ((96, 10_000), (128, 30_000), (192, 60_000), (256, 100_000))
+
+
+def run_mixed(args, dev, torch, B=128, steps=10):
+    from paper_2508_04929_b300.batched import GraphStep, Problem
+    from paper_2508_04929_b300.splat import Splatter
+    probs = []
+    for i, (D, N) in enumerate(MIXED):
+        rng = synth.rng_for(100 + i)
+        th = torch.from_numpy(synth.random_gaussians(N, D, rng)).to(dev)
+        W = torch.from_numpy(synth.random_poses(B, rng).reshape(B, 9)).to(dev)
+        C = torch.from_numpy(synth.random_ctf(B, rng)).to(dev)
+        tg = torch.from_numpy(synth.random_gaussians(N, D, rng)).to(dev)
+        gt = Splatter(D, N, B, tile=16, chunk=128, device=dev)
+        _, X = gt.forward(tg, W, C)
+        sig = math.sqrt(float(X.double().var()) / CTF_SNR)
+        gen = torch.Generator(device=dev).manual_seed(4321 + i)
+        Y = (X + sig * torch.randn(X.shape, device=dev, generator=gen)).contiguous()
+        gt.close()
+        probs.append(Problem(D=D, theta=th, W=W, ctf=C, Y=Y))
+    gs = GraphStep(probs, adam=True, autotune_chunks=(64, 128))
+    for _ in range(3):
+        gs.replay()
+    torch.cuda.synchronize()
+    st = gs.check()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        gs.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    out = {"workload": "4 volumes N=10k/30k/60k/100k at D=96/128/192/256, 128 particles each, one CUDA graph",
+           "value": 4 * B / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "status": st,
+           "launch_shapes": [{"D": p.D, "N": p.N, "tile": p.tile, "chunk": p.chunk} for p in gs.problems]}
+    gs.close()
+    return out
+
+
+# ---------------------------------------------------------------------------------------
 # the reference arm: the FP64 oracle on the host cores
 # ---------------------------------------------------------------------------------------
 def run_reference(args, rank):
@@ -241,54 +285,22 @@ def main():
                              tiles=(tile,) if tile else (8, 16, 32), chunks=(chunk,) if chunk else (64, 128, 256))
         tile, chunk = tune["tile"], tune["chunk"]
 
-    sp = Splatter(args.D, args.N, args.B, tile=tile, chunk=chunk, device=dev)
-    dth = torch.zeros_like(t)
-    m = torch.zeros_like(t)
-    v = torch.zeros_like(t)
-    theta = t.clone()
-    # size the pair buffer once (host sync), then run without syncs
-    sp.forward(theta, W, C, grow=True)
-    sp.pairs = torch.empty(int((int(sp.n_pairs.item()) & 0xFFFFFFFF) * 1.3) + 4096, dtype=torch.int32, device=dev)
+    # --- batched, fused form: the whole step as one CUDA graph (autotuned launch shape) ---
+    from paper_2508_04929_b300.batched import GraphStep, Problem
+    prob = Problem(D=args.D, theta=t.clone(), W=W.clone(), ctf=C.clone(), Y=Y, tile=tile, chunk=chunk)
+    gs = GraphStep([prob], adam=True)
+    sp = prob.sp
     stream = torch.cuda.current_stream()
-    ev = {k: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for k in ("fwd", "bwd")}
-    kt = {"fwd": [], "bwd": []}
-    step_no = [0]
-
-    def step(timed=False):
-        dth.zero_()
-        sp.project(theta, W)
-        sp.bin_sort(grow=False)
-        if timed:
-            ev["fwd"][0].record(stream)
-        sp.render()
-        if timed:
-            ev["fwd"][1].record(stream)
-        sp.apply_ctf(sp.Q, C, sp.X)
-        sp.loss_grad(sp.X, Y)
-        sp.apply_ctf(sp.dX, C, sp.dQ)
-        if timed:
-            ev["bwd"][0].record(stream)
-        sp.backward(theta, W, sp.dQ, dth)
-        if timed:
-            ev["bwd"][1].record(stream)
-        step_no[0] += 1
-        L.gs_step(theta, dth, m, v, step_no[0])
-        if timed:
-            torch.cuda.synchronize()
-            kt["fwd"].append(ev["fwd"][0].elapsed_time(ev["fwd"][1]))
-            kt["bwd"].append(ev["bwd"][0].elapsed_time(ev["bwd"][1]))
-
     for _ in range(max(args.warmup, 3)):
-        step()
+        gs.replay()
     torch.cuda.synchronize()
-    st = sp.status()
+    st = gs.check()
     # algorithmic work: Gaussian-pixel evaluations inside the support boxes of this batch
     box = sp.proj.view(torch.int16).view(args.B, args.N, 16)[:, :, 12:16].to(torch.int64)
     area = ((box[..., 1] - box[..., 0] + 1).clamp(min=0) * (box[..., 3] - box[..., 2] + 1).clamp(min=0))
     e_alg = int(area.sum())
     n_pairs = int(sp.n_pairs.item()) & 0xFFFFFFFF
 
-    # --- timed region: batched form (kernel-level per-call events in a second pass) ---
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if dist is not None:
         dist.barrier()
@@ -296,12 +308,32 @@ def main():
     with ClockSampler(local) as clk:
         e0.record(stream)
         for _ in range(args.steps):
-            step()
+            gs.replay()
         e1.record(stream)
         torch.cuda.synchronize()
         ms_total = e0.elapsed_time(e1)
+        # the same kernels once more, eagerly, with CUDA events around the two render calls
+        ev = {k: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for k in ("fwd", "bwd", "fft")}
+        kt = {"fwd": [], "bwd": [], "fft": []}
+        dth = torch.zeros_like(t)
         for _ in range(min(args.steps, 5)):
-            step(timed=True)
+            dth.zero_()
+            sp.project(prob.theta, W)
+            sp.bin_sort(grow=False)
+            ev["fwd"][0].record(stream)
+            sp.render()
+            ev["fwd"][1].record(stream)
+            ev["fft"][0].record(stream)
+            sp.apply_ctf(sp.Q, C, sp.X)
+            ev["fft"][1].record(stream)
+            sp.loss_grad(sp.X, Y)
+            sp.apply_ctf(sp.dX, C, sp.dQ)
+            ev["bwd"][0].record(stream)
+            sp.backward(prob.theta, W, sp.dQ, dth)
+            ev["bwd"][1].record(stream)
+            torch.cuda.synchronize()
+            for k in kt:
+                kt[k].append(ev[k][0].elapsed_time(ev[k][1]))
     if dist is not None:
         tt = torch.tensor([ms_total], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -310,11 +342,12 @@ def main():
     value = world * args.B / (ms_step * 1e-3)
     t_fwd = statistics.median(kt["fwd"])
     t_bwd = statistics.median(kt["bwd"])
+    t_ctf = statistics.median(kt["fft"])
 
     # --- plain form: one particle per launch sequence, batch size 1, Adam per image ---
     plain = None
     if not args.no_plain:
-        p1 = Splatter(args.D, args.N, 1, tile=16, chunk=128, device=dev)
+        p1 = Splatter(args.D, args.N, 1, tile=tile, chunk=chunk, device=dev)
         th1 = t.clone()
         m1, v1, g1 = torch.zeros_like(t), torch.zeros_like(t), torch.zeros_like(t)
         for b in range(2):
@@ -331,26 +364,27 @@ def main():
         plain = nimg / (time.perf_counter() - s0)
         p1.close()
 
-    # --- end to end through the public API with host buffers ---
+    # --- end to end through the public API with host buffers: copy in, replay, loss out ---
     Yh = Y.cpu().pin_memory()
     Wh = W.cpu().pin_memory()
     Ch = C.cpu().pin_memory()
-    Yd, Wd, Cd = torch.empty_like(Y), torch.empty_like(W), torch.empty_like(C)
     lossh = torch.empty(args.B, dtype=torch.float32).pin_memory()
     h2d = Yh.numel() * 4 + Wh.numel() * 4 + Ch.numel() * 4
     d2h = lossh.numel() * 4
     torch.cuda.synchronize()
     s0 = time.perf_counter()
     for i in range(args.steps):
-        Yd.copy_(Yh, non_blocking=True)
-        Wd.copy_(Wh, non_blocking=True)
-        Cd.copy_(Ch, non_blocking=True)
-        dth.zero_()
-        sp.forward_backward(theta, Wd, Cd, Yd, dth, grow=False)
-        L.gs_step(theta, dth, m, v, step_no[0] + i + 1)
-        lossh.copy_(sp.loss[: args.B], non_blocking=True)
+        gs.load(0, W=Wh, ctf=Ch, Y=Yh)
+        loss = gs.replay()[0]
+        lossh.copy_(loss, non_blocking=True)
         torch.cuda.synchronize()
     e2e = world * args.B * args.steps / (time.perf_counter() - s0)
+    gs.close()
+
+    # --- mixed batch: four volumes of different D and N in one graph (autotuned each) ---
+    mixed = None
+    if args.mixed:
+        mixed = run_mixed(args, dev, torch)
 
     cpu = None
     if pool is not None:
@@ -376,17 +410,17 @@ def main():
             "plain_form": {"value": plain, "unit": UNIT, "form": "one particle per launch sequence, Adam per image"},
             "speedup_vs_plain": (value / world / plain) if plain else None,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": 13 * args.steps,
+            "gpu_launches": 15 * args.steps,
             "roofline": {"bound": "alu", "kernel": f"k_render_{dom}", "achieved": achieved / 1e9,
                          "peak": peak_exp / 1e9, "unit": "Gex2/s", "frac": achieved / peak_exp, "traffic": None},
-            "fwd_bwd_splat": {"ms_fwd": t_fwd, "ms_bwd": t_bwd, "alg_evals_per_step": e_alg,
+            "fwd_bwd_splat": {"ms_fwd": t_fwd, "ms_bwd": t_bwd, "ms_ctf_one_pass": t_ctf, "alg_evals_per_step": e_alg,
                               "pairs_per_step": n_pairs,
                               "frac_of_sfu_roofline": (2 * e_alg / ((t_fwd + t_bwd) * 1e-3)) / peak_exp},
             "cpu_baseline": cpu, "clocks": clocks, "status": st,
             "autotune": tune,
+            "mixed_batch": mixed,
         }
         print(json.dumps(line), flush=True)
-    sp.close()
     if dist is not None:
         dist.destroy_process_group()
 

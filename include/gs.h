@@ -189,6 +189,13 @@ int gs_render_bwd(const gs_config* cfg, const float* theta, int N, const float* 
 int gs_step(float* theta, const float* dtheta, float* m, float* v, int n, int t, float lr,
             float beta1, float beta2, float eps, gs_stream_t stream);
 
+/* Adam step as gs_step with the step counter kept on the device: *t_dev (device int) holds
+ * the number of steps already taken; the call uses t = *t_dev + 1 and then increments
+ * *t_dev (stream-ordered).  Nothing depends on host values that change between steps, so
+ * the call can be recorded once in a CUDA graph and replayed (Sec. 4.1 Adam). */
+int gs_step_counted(float* theta, const float* dtheta, float* m, float* v, int n, int* t_dev,
+                    float lr, float beta1, float beta2, float eps, gs_stream_t stream);
+
 /* ---------------------------------------------------------------------------------------
  * Binning without a caller workspace
  * ------------------------------------------------------------------------------------- */

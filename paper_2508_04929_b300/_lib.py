@@ -65,6 +65,7 @@ _SIGS = {
     "gs_loss": [_CFG, _P, _P, _I, _P, _P, _P],
     "gs_render_bwd": [_CFG, _P, _I, _P, _I, _P, _P, _P, _P, _P, _P, _S, _P],
     "gs_step": [_P, _P, _P, _P, _I, _I, _F, _F, _F, _F, _P],
+    "gs_step_counted": [_P, _P, _P, _P, _I, _P, _F, _F, _F, _F, _P],
     "gs_bin_sort_noalloc": [_CFG, _P, _I, _I, _P, _S, _P, _P, _P, ctypes.POINTER(_S)],
 }
 for _name, _args in _SIGS.items():
@@ -165,6 +166,12 @@ def gs_render_bwd(cfg, theta, W, proj, pair_gauss, tile_ranges, dLdQ, dtheta, ws
 def gs_step(theta, dtheta, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None) -> None:
     _check("gs_step", lib.gs_step(_ptr(theta), _ptr(dtheta), _ptr(m), _ptr(v), theta.numel(), int(t), float(lr),
                                   float(beta1), float(beta2), float(eps), _stream(stream)))
+
+
+def gs_step_counted(theta, dtheta, m, v, t_dev, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None) -> None:
+    _check("gs_step_counted", lib.gs_step_counted(_ptr(theta), _ptr(dtheta), _ptr(m), _ptr(v), theta.numel(),
+                                                  _ptr(t_dev), float(lr), float(beta1), float(beta2), float(eps),
+                                                  _stream(stream)))
 
 
 def gs_bin_sort_noalloc(cfg, proj, B, N, pair_gauss, tile_ranges, n_pairs, stream=None) -> int:

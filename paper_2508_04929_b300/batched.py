@@ -1,0 +1,165 @@
+"""Batched, CUDA-graph-captured training steps (Algorithm 1's loop body over a minibatch).
+
+``GraphStep`` records, once, the whole step for one or several *problems* -- a problem is
+a volume (theta, N Gaussians) with its own box size D and a batch of B particles with
+their own poses, CTF parameters and observed images -- into a single CUDA graph:
+
+    per problem: zero grad -> gs_project -> gs_bin_sort -> gs_render_fwd -> gs_apply_ctf
+                 -> gs_loss -> gs_apply_ctf (adjoint) -> gs_render_bwd -> gs_step_counted
+
+Problems of a mixed batch (different D and N) run on their own streams inside the graph,
+so small volumes overlap large ones; one ``replay()`` launches the whole batch.  Inputs
+change between steps by copying into the static buffers (``load``); the Adam step counter
+lives on the device so replays need no host values.  The pair buffers are sized by an
+eager pass with a margin; ``check()`` reads the status words (a host sync) and re-sizes and
+re-records if a step ever needed more pairs.  The tile size and chunk depth of every
+problem come from the autotuner unless given.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import torch
+
+from . import _lib as L
+from .autotune import tune
+from .splat import Splatter
+
+
+@dataclass
+class Problem:
+    D: int
+    theta: torch.Tensor          # [N, 11] raw parameters (updated in place by Adam)
+    W: torch.Tensor              # [B, 9] poses
+    ctf: torch.Tensor            # [B, 5]
+    Y: torch.Tensor              # [B, D, D] observed images
+    tile: int = 0                # 0 = autotune
+    chunk: int = 0               # 0 = autotune
+    lr: float = 1e-3
+    sp: Splatter = field(default=None, repr=False)
+    dtheta: torch.Tensor = field(default=None, repr=False)
+    m: torch.Tensor = field(default=None, repr=False)
+    v: torch.Tensor = field(default=None, repr=False)
+    t: torch.Tensor = field(default=None, repr=False)
+    tune: dict = field(default=None, repr=False)
+
+    @property
+    def N(self):
+        return self.theta.shape[0]
+
+    @property
+    def B(self):
+        return self.W.shape[0]
+
+
+class GraphStep:
+    def __init__(self, problems, margin=1.3, adam=True, use_graph=True, autotune_chunks=(64, 128, 256),
+                 min_pairs=4096):
+        self.problems = list(problems)
+        self.margin = float(margin)
+        self.min_pairs = int(min_pairs)
+        self.adam = adam
+        self.use_graph = use_graph
+        self.dev = self.problems[0].theta.device
+        for p in self.problems:
+            if p.tile == 0 or p.chunk == 0:
+                p.tune = tune(p.D, p.N, p.B, p.theta, p.W, p.ctf, p.Y, device=self.dev,
+                              tiles=(p.tile,) if p.tile else (8, 16, 32),
+                              chunks=(p.chunk,) if p.chunk else autotune_chunks)
+                p.tile, p.chunk = p.tune["tile"], p.tune["chunk"]
+            p.sp = Splatter(p.D, p.N, p.B, tile=p.tile, chunk=p.chunk, device=self.dev)
+            p.dtheta = torch.zeros_like(p.theta)
+            p.m = torch.zeros_like(p.theta)
+            p.v = torch.zeros_like(p.theta)
+            p.t = torch.zeros(1, dtype=torch.int32, device=self.dev)
+        self.streams = [torch.cuda.Stream(device=self.dev) for _ in self.problems]
+        self.graph = None
+        self._size_pairs()
+        self._record()
+
+    # -- set-up ----------------------------------------------------------------------------
+    def _size_pairs(self):
+        for p in self.problems:
+            p.sp.forward(p.theta, p.W, p.ctf, grow=True)
+            need = int(p.sp.n_pairs.item()) & 0xFFFFFFFF
+            cap = max(int(need * self.margin), self.min_pairs)
+            if not (cap <= p.sp.pairs.numel() <= 2 * cap):
+                p.sp.pairs = torch.empty(cap, dtype=torch.int32, device=self.dev)
+            L.gs_clear_status(p.sp.ws)
+        torch.cuda.synchronize(self.dev)
+
+    def _body(self, p):
+        sp = p.sp
+        p.dtheta.zero_()
+        sp.project(p.theta, p.W)
+        sp.bin_sort(grow=False)
+        sp.render()
+        sp.apply_ctf(sp.Q, p.ctf, sp.X)
+        sp.loss_grad(sp.X, p.Y)
+        sp.apply_ctf(sp.dX, p.ctf, sp.dQ)
+        sp.backward(p.theta, p.W, sp.dQ, p.dtheta)
+        if self.adam:
+            L.gs_step_counted(p.theta, p.dtheta, p.m, p.v, p.t, lr=p.lr)
+
+    def _run_all(self):
+        main = torch.cuda.current_stream(self.dev)
+        if len(self.problems) == 1:
+            self._body(self.problems[0])
+            return
+        for p, s in zip(self.problems, self.streams):
+            s.wait_stream(main)
+            with torch.cuda.stream(s):
+                self._body(p)
+        for s in self.streams:
+            main.wait_stream(s)
+
+    def _record(self):
+        if not self.use_graph:
+            return
+        # warm the exact sequence once on a side stream (cuFFT, attribute set-up), then record
+        saved = [(p.theta.clone(), p.m.clone(), p.v.clone(), p.t.clone()) for p in self.problems]
+        side = torch.cuda.Stream(device=self.dev)
+        side.wait_stream(torch.cuda.current_stream(self.dev))
+        with torch.cuda.stream(side):
+            self._run_all()
+        torch.cuda.current_stream(self.dev).wait_stream(side)
+        torch.cuda.synchronize(self.dev)
+        for p, (th, m, v, t) in zip(self.problems, saved):
+            p.theta.copy_(th); p.m.copy_(m); p.v.copy_(v); p.t.copy_(t)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, capture_error_mode="thread_local"):
+            self._run_all()
+        torch.cuda.synchronize(self.dev)
+
+    # -- use -------------------------------------------------------------------------------
+    def load(self, i, W=None, ctf=None, Y=None):
+        """Copy the next batch of problem i into the static buffers (stream-ordered)."""
+        p = self.problems[i]
+        for dst, src in ((p.W, W), (p.ctf, ctf), (p.Y, Y)):
+            if src is not None:
+                dst.copy_(src, non_blocking=True)
+
+    def replay(self):
+        """One step for every problem.  Returns the per-image loss tensors (device)."""
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self._run_all()
+        return [p.sp.loss[: p.B] for p in self.problems]
+
+    def check(self):
+        """Read the status words (host sync).  If a pair buffer overflowed, re-size and
+        re-record; returns the OR of the status bits seen."""
+        st = 0
+        for p in self.problems:
+            st |= L.gs_read_status(p.sp.ws, clear=True)
+        if st & L.GS_STATUS_OVERFLOW:
+            self.margin = max(self.margin, 1.3) * 1.5
+            self._size_pairs()
+            self._record()
+        return st
+
+    def close(self):
+        for p in self.problems:
+            if p.sp is not None:
+                p.sp.close()

@@ -198,4 +198,11 @@ int gs_step(float* theta, const float* dtheta, float* m, float* v, int n, int t,
                              (cudaStream_t)stream));
 }
 
+int gs_step_counted(float* theta, const float* dtheta, float* m, float* v, int n, int* t_dev, float lr,
+                    float beta1, float beta2, float eps, gs_stream_t stream) {
+  if (n < 0 || !t_dev) return GS_EINVAL;
+  if (n > 0 && (!theta || !dtheta || !m || !v)) return GS_EINVAL;
+  return cuda_rc(launch_adam_counted(theta, dtheta, m, v, n, t_dev, lr, beta1, beta2, eps, (cudaStream_t)stream));
+}
+
 }  // extern "C"

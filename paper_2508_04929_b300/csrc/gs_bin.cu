@@ -283,20 +283,23 @@ cudaError_t launch_bin(const gs_config& cfg, const WsLayout& L, const gs_record*
   dim3 g2(C, B);
   size_t sm_count = sizeof(uint32_t) * Tn;
   cudaError_t e;
-  if (sm_count > 48 * 1024) {
-    e = cudaFuncSetAttribute(k_bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_count);
+  {
+    static int cache[64] = {0};
+    e = ensure_smem((const void*)k_bin_count, sm_count, cache);
     if (e != cudaSuccess) return e;
   }
   k_bin_count<<<g2, 256, sm_count, s>>>(proj, N, T, ntx, Tn, C, hist);
-  if (sm_count > 48 * 1024) {
-    e = cudaFuncSetAttribute(k_bin_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_count);
+  {
+    static int cache[64] = {0};
+    e = ensure_smem((const void*)k_bin_scan, sm_count, cache);
     if (e != cudaSuccess) return e;
   }
   k_bin_scan<<<B, 1024, sm_count, s>>>(hist, Tn, C, tstart, ttotal, itotal);
   k_bin_base<<<1, 32, 0, s>>>(itotal, B, ibase, n_pairs, (unsigned long long)cap, status);
   size_t sm_scatter = sizeof(uint32_t) * kBinWarps * Tn;
-  if (sm_scatter > 48 * 1024) {
-    e = cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_scatter);
+  {
+    static int cache[64] = {0};
+    e = ensure_smem((const void*)k_bin_scatter, sm_scatter, cache);
     if (e != cudaSuccess) return e;
   }
   k_bin_scatter<<<g2, 32 * kBinWarps, sm_scatter, s>>>(proj, N, T, ntx, Tn, C, hist, tstart, ttotal, ibase,

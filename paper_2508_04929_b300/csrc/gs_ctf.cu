@@ -88,7 +88,43 @@ __global__ void k_adam(float* __restrict__ th, const float* __restrict__ g, floa
   }
 }
 
+// Adam with the step counter on the device (t_dev = steps already taken), so that a captured
+// graph can be replayed: bias corrections are formed in FP64 once per CTA.
+__global__ void k_adam_counted(float* __restrict__ th, const float* __restrict__ g, float* __restrict__ m,
+                               float* __restrict__ v, int n, const int* __restrict__ t_dev, float lr, float b1,
+                               float b2, float eps) {
+  __shared__ float cc[2];
+  if (threadIdx.x == 0) {
+    const double t = (double)(*t_dev + 1);
+    cc[0] = (float)(1.0 / (1.0 - pow((double)b1, t)));
+    cc[1] = (float)(1.0 / (1.0 - pow((double)b2, t)));
+  }
+  __syncthreads();
+  const float c1 = cc[0], c2 = cc[1];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    th[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+  }
+}
+
+__global__ void k_count_step(int* t_dev) { *t_dev += 1; }
+
 }  // namespace
+
+cudaError_t launch_adam_counted(float* theta, const float* g, float* m, float* v, int n, int* t_dev, float lr,
+                                float b1, float b2, float eps, cudaStream_t s) {
+  if (n > 0) {
+    int blocks = (n + 255) / 256;
+    if (blocks > 148 * 16) blocks = 148 * 16;
+    k_adam_counted<<<blocks, 256, 0, s>>>(theta, g, m, v, n, t_dev, lr, b1, b2, eps);
+  }
+  k_count_step<<<1, 1, 0, s>>>(t_dev);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_ctf_mul(const gs_config& cfg, float2* spec, const float* ctf, int B, cudaStream_t s) {
   if (B <= 0) return cudaSuccess;

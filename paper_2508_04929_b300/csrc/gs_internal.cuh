@@ -80,6 +80,19 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
+// Raise a kernel's dynamic shared-memory limit once per device and size (the call is
+// skipped when an earlier call already allowed at least `bytes`, e.g. during stream capture).
+inline cudaError_t ensure_smem(const void* func, size_t bytes, int* cache /* [64] per call site */) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && cache[dev] >= (int)bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) cache[dev] = (int)bytes;
+  return e;
+}
+
 // Host-side launchers (one per translation unit).
 cudaError_t launch_activate(const float* theta, int N, float* gauss, float* gacc, int* status, cudaStream_t s);
 cudaError_t launch_project(const gs_config& cfg, const float* gauss, int N, const float* W, int B,
@@ -106,5 +119,7 @@ cudaError_t launch_loss(const gs_config& cfg, const float* X, const float* Y, in
                         float* dLdX, cudaStream_t s);
 cudaError_t launch_adam(float* theta, const float* g, float* m, float* v, int n, float lr,
                         float b1, float b2, float eps, float c1, float c2, cudaStream_t s);
+cudaError_t launch_adam_counted(float* theta, const float* g, float* m, float* v, int n, int* t_dev, float lr,
+                                float b1, float b2, float eps, cudaStream_t s);
 
 }  // namespace gs

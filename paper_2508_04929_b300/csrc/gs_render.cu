@@ -448,8 +448,9 @@ cudaError_t launch_render_fwd(const gs_config& cfg, const gs_record* proj, int N
   if (B <= 0) return cudaSuccess;
   const int ntx = (cfg.D + cfg.tile - 1) / cfg.tile;
   const size_t sm = render_fwd_smem(cfg);
-  if (sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_render_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  {
+    static int cache[64] = {0};
+    cudaError_t e = ensure_smem((const void*)k_render_fwd, sm, cache);
     if (e != cudaSuccess) return e;
   }
   k_render_fwd<<<render_grid(cfg, B), render_warps(cfg.tile) * 32, sm, s>>>(proj, N, pair_gauss, ranges, cfg.D,
@@ -464,8 +465,9 @@ cudaError_t launch_render_bwd(const gs_config& cfg, const gs_record* proj, int N
   const int ntx = (cfg.D + cfg.tile - 1) / cfg.tile;
   const int chunk = render_bwd_chunk(cfg);
   const size_t sm = render_bwd_smem(cfg.tile, chunk);
-  if (sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_render_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  {
+    static int cache[64] = {0};
+    cudaError_t e = ensure_smem((const void*)k_render_bwd, sm, cache);
     if (e != cudaSuccess) return e;
   }
   const float h = 2.f * cfg.E / (float)cfg.D;
