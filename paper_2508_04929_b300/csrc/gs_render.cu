@@ -4,15 +4,15 @@
 // tiles of 8 or 16 pixels, a 16 x 16 quadrant of a 32-pixel tile) and stages the tile's
 // Gaussian records through shared memory in chunks.  Each warp owns one 4 x 4 pixel block
 // of the region.  For every chunk a warp compacts, with ballots, the records whose support
-// box touches its block into a per-warp list; the lanes then take different list entries
-// ("items" = one Gaussian on one block) and each lane evaluates its Gaussian on the block's
-// 16 pixels.  The work executed is therefore that of 4 x 4 blocks (1.76x the algorithmic
+// box touches its block into a per-warp list (the forward tests a block mask formed once per
+// record while staging); the lanes then take different list entries ("items" = one Gaussian
+// on one block) and each lane evaluates its Gaussian on the block's 16 pixels.  The work executed is therefore that of 4 x 4 blocks (1.76x the algorithmic
 // Gaussian-pixel count on the bench workload, against 3.1x for 8 x 8 warp regions).
 //
-// Per item a lane forms the exponent E(u, v) = ca (dx0+u)^2 + cb (dx0+u)(dy0+v) +
-// cc (dy0+v)^2 by forward differences along u and v, takes one ex2.approx per pixel, and
-// masks the pixels outside the support box (box columns as predicates, box rows as zero
-// weights).
+// Per item a lane forms the row start values of the exponent E(u, v) = ca (dx0+u)^2 +
+// cb (dx0+u)(dy0+v) + cc (dy0+v)^2 and runs the multiplicative recurrence described at
+// for_block_values (two rows per f32x2 instruction), masking the pixels outside the support
+// box (box columns as predicates, box rows as zero start values).
 //
 // Forward: each lane accumulates its items' contributions to the 16 pixels in registers; at
 // the end the 32 partial sums of each pixel are added by a transposing butterfly (16
@@ -134,80 +134,231 @@ __device__ __forceinline__ Mask make_mask(const Rec& r, int X, int Y, float w) {
   return m;
 }
 
+// Region of a CTA: origin, side (8 or 16 pixels) and blocks per side.
+struct Region {
+  int RX, RY, S, bs;
+};
+
+__device__ __forceinline__ Region region_of(int T, int ntx, int tile, int sub) {
+  Region r;
+  r.S = T == 32 ? 16 : T;
+  r.bs = r.S / kBlk;
+  r.RX = (tile % ntx) * T + (sub & 1) * 16;
+  r.RY = (tile / ntx) * T + (sub >> 1) * 16;
+  return r;
+}
+
+// Bit j = by * bs + bx set iff the box touches block (bx, by) of the region.
+__device__ __forceinline__ unsigned block_mask(int x0, int x1, int y0, int y1, const Region& g) {
+  const int lx = max(x0 - g.RX, 0), hx = min(x1 - g.RX, g.S - 1);
+  const int ly = max(y0 - g.RY, 0), hy = min(y1 - g.RY, g.S - 1);
+  if (lx > hx || ly > hy) return 0u;
+  const int bx0 = lx >> 2, bx1 = hx >> 2, by0 = ly >> 2, by1 = hy >> 2;
+  const unsigned cols = ((2u << bx1) - 1u) & ~((1u << bx0) - 1u);
+  unsigned m = 0u;
+  for (int by = by0; by <= by1; ++by) m |= cols << (by * g.bs);
+  return m;
+}
+
+// Stage records [start, start + n) of the tile list and their block masks.
+__device__ __forceinline__ void stage_chunk_masked(gs_record* rec, uint16_t* msk, const gs_record* __restrict__ proj,
+                                                   size_t pbase, const uint32_t* __restrict__ pair_gauss,
+                                                   uint32_t start, int n, const Region& reg) {
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const uint32_t g = pair_gauss[start + k];
+    const float4* src = reinterpret_cast<const float4*>(proj + pbase + g);
+    float4* dst = reinterpret_cast<float4*>(rec + k);
+    const float4 a = __ldg(src), b = __ldg(src + 1);
+    dst[0] = a;
+    dst[1] = b;
+    const int bx = __float_as_int(b.z), by = __float_as_int(b.w);
+    msk[k] = (uint16_t)block_mask((int)(int16_t)(bx & 0xffff), bx >> 16, (int)(int16_t)(by & 0xffff), by >> 16, reg);
+  }
+}
+
+// Ballot compaction of the chunk's records whose mask has bit `blk`: writes their indices
+// to list[0..cnt) in index order and returns cnt (warp-uniform).
+__device__ __forceinline__ int compact_mask(const uint16_t* msk, int n, int blk, uint16_t* list) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  int cnt = 0;
+  for (int base = 0; base < n; base += 32) {
+    const int k = base + lane;
+    const bool hit = k < n && ((msk[k] >> blk) & 1u);
+    const unsigned m = __ballot_sync(0xffffffffu, hit);
+    if (hit) list[cnt + __popc(m & lt)] = (uint16_t)k;
+    cnt += __popc(m);
+  }
+  __syncwarp();
+  return cnt;
+}
+
+// ---------------------------------------------------------------------------------------
+// Item evaluation.  Rows v = 0..3 of the block are handled in packed pairs (0,1) and (2,3)
+// with the f32x2 instructions of sm_100+ (two lanes of work per instruction).
+//
+// Along a row the exponent is quadratic in u, so the value follows the recurrence
+//   V(u+1) = V(u) R(u),  R(u+1) = R(u) 2^(2 ca),   V(0) = 2^E(0,v), R(0) = 2^D(0,v),
+// with E(0,v) the exponent at the block's first column and D(0,v) = E(1,v) - E(0,v): nine
+// ex2 per item instead of sixteen, and two multiplies per packed pixel pair.  The recurrence
+// is used when V(0) cannot underflow and R(0) cannot overflow (E(0,v) > -100, D(0,v) < 100,
+// which holds for every Gaussian wider than ~0.35 px); otherwise the item takes the exact
+// path (one ex2 per pixel of the exponent formed by forward differences).  Rows outside the
+// support box start at V(0) = 0 (and stay 0); columns outside it are skipped by predicates.
+// ---------------------------------------------------------------------------------------
+typedef unsigned long long u64;
+
+__device__ __forceinline__ u64 pk(float a, float b) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk(u64 r, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+  u64 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+  u64 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+  u64 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// Start exponents E(0,v) and first differences D(0,v) of the 4 rows of a block whose
+// corner is (dx0, dy0) pixels from the Gaussian centre.
+struct RowStart {
+  float E[kBlk], D[kBlk];
+};
+
+__device__ __forceinline__ RowStart row_start(const Rec& r, float dx0, float dy0) {
+  RowStart s;
+  float G = fmaf(r.cb, dx0, r.cc * (2.f * dy0 + 1.f));
+  s.E[0] = fmaf(dx0, fmaf(r.ca, dx0, r.cb * dy0), r.cc * dy0 * dy0);
+  s.D[0] = fmaf(r.ca, 2.f * dx0 + 1.f, r.cb * dy0);
+#pragma unroll
+  for (int v = 1; v < kBlk; ++v) {
+    s.E[v] = s.E[v - 1] + G;
+    G = fmaf(2.f, r.cc, G);
+    s.D[v] = s.D[v - 1] + r.cb;
+  }
+  return s;
+}
+
+__device__ __forceinline__ bool recurrence_safe(const RowStart& s) {
+  const float emin = fminf(fminf(s.E[0], s.E[1]), fminf(s.E[2], s.E[3]));
+  const float dmax = fmaxf(fmaxf(s.D[0], s.D[1]), fmaxf(s.D[2], s.D[3]));
+  return emin > -100.f && dmax < 100.f;
+}
+
+// Values of the 4 rows (as two packed pairs) at every column u of the block, handed to
+// body(u, v01, v23).  rowscale[v] multiplies row v (0 for rows outside the box).
+template <class Body>
+__device__ __forceinline__ void for_block_values(const Rec& r, const RowStart& s, const float rowscale[kBlk],
+                                                 Body body) {
+  if (recurrence_safe(s)) {
+    u64 V01 = pk(rowscale[0] * ex2_approx(s.E[0]), rowscale[1] * ex2_approx(s.E[1]));
+    u64 V23 = pk(rowscale[2] * ex2_approx(s.E[2]), rowscale[3] * ex2_approx(s.E[3]));
+    u64 R01 = pk(ex2_approx(s.D[0]), ex2_approx(s.D[1]));
+    u64 R23 = pk(ex2_approx(s.D[2]), ex2_approx(s.D[3]));
+    const float st = ex2_approx(2.f * r.ca);
+    const u64 S = pk(st, st);
+#pragma unroll
+    for (int u = 0; u < kBlk; ++u) {
+      body(u, V01, V23);
+      if (u + 1 < kBlk) {
+        V01 = mul2(V01, R01);
+        V23 = mul2(V23, R23);
+        if (u + 2 < kBlk) {
+          R01 = mul2(R01, S);
+          R23 = mul2(R23, S);
+        }
+      }
+    }
+  } else {
+    float e[kBlk], d[kBlk];
+#pragma unroll
+    for (int v = 0; v < kBlk; ++v) { e[v] = s.E[v]; d[v] = s.D[v]; }
+    const float two_a = 2.f * r.ca;
+#pragma unroll
+    for (int u = 0; u < kBlk; ++u) {
+      const u64 V01 = pk(rowscale[0] * ex2_approx(e[0]), rowscale[1] * ex2_approx(e[1]));
+      const u64 V23 = pk(rowscale[2] * ex2_approx(e[2]), rowscale[3] * ex2_approx(e[3]));
+      body(u, V01, V23);
+#pragma unroll
+      for (int v = 0; v < kBlk; ++v) { e[v] += d[v]; d[v] += two_a; }
+    }
+  }
+}
+
 __global__ void k_render_fwd(const gs_record* __restrict__ proj, int N, const uint32_t* __restrict__ pair_gauss,
                              const uint32_t* __restrict__ ranges, int D, int T, int ntx, int chunk,
                              float* __restrict__ Q) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   gs_record* rec = reinterpret_cast<gs_record*>(smem_raw);
-  uint16_t* list = reinterpret_cast<uint16_t*>(smem_raw + sizeof(gs_record) * chunk) + warp * chunk;
+  uint16_t* msk = reinterpret_cast<uint16_t*>(smem_raw + sizeof(gs_record) * chunk);
+  uint16_t* list = msk + chunk + warp * chunk;
   const int regions = T == 32 ? 4 : 1;
   const int tile = blockIdx.x / regions, sub = blockIdx.x % regions, b = blockIdx.y, Tn = ntx * ntx;
   const Geo geo = geometry(T, ntx, tile, sub);
+  const Region reg = region_of(T, ntx, tile, sub);
   const uint32_t start = ranges[((size_t)b * Tn + tile) * 2], end = ranges[((size_t)b * Tn + tile) * 2 + 1];
   const size_t pbase = (size_t)b * N;
   const float fX = (float)geo.X, fY = (float)geo.Y;
-  float acc[kBlk][kBlk];
+  u64 acc01[kBlk], acc23[kBlk];  // (row 0, row 1) and (row 2, row 3) of column u
 #pragma unroll
-  for (int v = 0; v < kBlk; ++v)
-#pragma unroll
-    for (int u = 0; u < kBlk; ++u) acc[v][u] = 0.f;
+  for (int u = 0; u < kBlk; ++u) acc01[u] = acc23[u] = pk(0.f, 0.f);
   int running = 0;
-  (void)nwarps;
   for (uint32_t base = start; base < end; base += chunk) {
     const int n = (int)min((uint32_t)chunk, end - base);
     __syncthreads();
-    stage_chunk(rec, proj, pbase, pair_gauss, base, n);
+    stage_chunk_masked(rec, msk, proj, pbase, pair_gauss, base, n, reg);
     __syncthreads();
-    const int cnt = compact(rec, n, geo.X, geo.Y, list, nullptr);
+    const int cnt = compact_mask(msk, n, warp, list);
     for (int i = (lane - running) & 31; i < cnt; i += 32) {
       const Rec r = load_rec(rec + list[i]);
       const Mask mk = make_mask(r, geo.X, geo.Y, r.w);
-      const float dx0 = fX - r.cx, dy0 = fY - r.cy;
-      const float two_a = 2.f * r.ca, two_c = 2.f * r.cc;
-      // row 0 start value and first differences along u (D) and v (G)
-      float E = fmaf(dx0, fmaf(r.ca, dx0, r.cb * dy0), r.cc * dy0 * dy0);
-      float Du = fmaf(r.ca, 2.f * dx0 + 1.f, r.cb * dy0);
-      float Gv = fmaf(r.cb, dx0, r.cc * (2.f * dy0 + 1.f));
-#pragma unroll
-      for (int v = 0; v < kBlk; ++v) {
-        float e = E, d = Du;
-#pragma unroll
-        for (int u = 0; u < kBlk; ++u) {
-          const float x = ex2_approx(e);
-          if (mk.col[u]) acc[v][u] = fmaf(mk.roww[v], x, acc[v][u]);
-          e += d;
-          d += two_a;
+      const RowStart rs = row_start(r, fX - r.cx, fY - r.cy);
+      for_block_values(r, rs, mk.roww, [&](int u, u64 v01, u64 v23) {
+        if (mk.col[u]) {
+          acc01[u] = add2(acc01[u], v01);
+          acc23[u] = add2(acc23[u], v23);
         }
-        E += Gv;
-        Gv += two_c;
-        Du += r.cb;
-      }
+      });
     }
     running = (running + cnt) & 31;
   }
+  float sv[16];
+#pragma unroll
+  for (int u = 0; u < kBlk; ++u) {
+    upk(acc01[u], sv[0 * kBlk + u], sv[1 * kBlk + u]);
+    upk(acc23[u], sv[2 * kBlk + u], sv[3 * kBlk + u]);
+  }
   // transposing butterfly: 16 values over 32 lanes
-  float s[16];
-#pragma unroll
-  for (int v = 0; v < kBlk; ++v)
-#pragma unroll
-    for (int u = 0; u < kBlk; ++u) s[v * kBlk + u] = acc[v][u];
 #pragma unroll
   for (int half = 8, off = 16; half >= 1; half >>= 1, off >>= 1) {
     const bool up = lane & off;
 #pragma unroll
     for (int k = 0; k < half; ++k) {
-      const float send = up ? s[k] : s[k + half];
-      const float keep = up ? s[k + half] : s[k];
-      s[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+      const float send = up ? sv[k] : sv[k + half];
+      const float keep = up ? sv[k + half] : sv[k];
+      sv[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
     }
   }
-  s[0] += __shfl_xor_sync(0xffffffffu, s[0], 1);
+  sv[0] += __shfl_xor_sync(0xffffffffu, sv[0], 1);
   // lane holds pixel p = (bit4 << 3) | (bit3 << 2) | (bit2 << 1) | bit1 of its lane index
   if ((lane & 1) == 0) {
     const int p = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
     const int i = geo.Y + p / kBlk, j = geo.X + p % kBlk;
-    if (i < D && j < D) Q[((size_t)b * D + i) * D + j] = s[0];
+    if (i < D && j < D) Q[((size_t)b * D + i) * D + j] = sv[0];
   }
 }
 
@@ -238,6 +389,12 @@ __global__ void k_render_bwd(const gs_record* __restrict__ proj, int N, const ui
       const int i = geo.Y + v, j = geo.X + u;
       g[v][u] = (i < D && j < D) ? dLdQ[((size_t)b * D + i) * D + j] : 0.f;
     }
+  u64 g01[kBlk], g23[kBlk];  // dL/dQ of the block as packed row pairs per column
+#pragma unroll
+  for (int u = 0; u < kBlk; ++u) {
+    g01[u] = pk(g[0][u], g[1][u]);
+    g23[u] = pk(g[2][u], g[3][u]);
+  }
   const float kap = -2.f / (kLog2e * h * h);  // P = kap * [[ca, -cb/2], [-cb/2, cc]]
   const float h2 = h * h;
   float* myres = res + (size_t)warp * chunk * 6;
@@ -251,40 +408,34 @@ __global__ void k_render_bwd(const gs_record* __restrict__ proj, int N, const ui
       const Rec r = load_rec(rec + list[i]);
       const Mask mk = make_mask(r, geo.X, geo.Y, 1.f);
       const float dx0 = fX - r.cx, dy0 = fY - r.cy;
-      const float two_a = 2.f * r.ca, two_c = 2.f * r.cc;
-      float E = fmaf(dx0, fmaf(r.ca, dx0, r.cb * dy0), r.cc * dy0 * dy0);
-      float Du = fmaf(r.ca, 2.f * dx0 + 1.f, r.cb * dy0);
-      float Gv = fmaf(r.cb, dx0, r.cc * (2.f * dy0 + 1.f));
+      // per row pair: sums over u of t, u t, u^2 t with t = dL/dQ * 2^E (masked)
+      u64 A01 = pk(0.f, 0.f), B01 = A01, C01 = A01, A23 = A01, B23 = A01, C23 = A01;
+      const RowStart rs = row_start(r, dx0, dy0);
+      for_block_values(r, rs, mk.roww, [&](int u, u64 v01, u64 v23) {
+        if (mk.col[u]) {
+          const u64 t01 = mul2(g01[u], v01), t23 = mul2(g23[u], v23);
+          A01 = add2(A01, t01);
+          A23 = add2(A23, t23);
+          if (u > 0) {
+            const u64 fu = pk((float)u, (float)u), fu2 = pk((float)(u * u), (float)(u * u));
+            B01 = fma2(fu, t01, B01);
+            B23 = fma2(fu, t23, B23);
+            C01 = fma2(fu2, t01, C01);
+            C23 = fma2(fu2, t23, C23);
+          }
+        }
+      });
+      float R0[kBlk], R1[kBlk], R2[kBlk];
+      upk(A01, R0[0], R0[1]); upk(A23, R0[2], R0[3]);
+      upk(B01, R1[0], R1[1]); upk(B23, R1[2], R1[3]);
+      upk(C01, R2[0], R2[1]); upk(C23, R2[2], R2[3]);
       // moments about the block origin: M0 = sum t, Mu = sum u t, Mv, Muu, Muv, Mvv
-      float M0 = 0.f, Mu = 0.f, Mv = 0.f, Muu = 0.f, Muv = 0.f, Mvv = 0.f;
-#pragma unroll
-      for (int v = 0; v < kBlk; ++v) {
-        float e = E, d = Du;
-        float t[kBlk];
-#pragma unroll
-        for (int u = 0; u < kBlk; ++u) {
-          const float x = ex2_approx(e);
-          t[u] = mk.col[u] ? g[v][u] * x : 0.f;
-          e += d;
-          d += two_a;
-        }
-        const float R0 = (t[0] + t[1]) + (t[2] + t[3]);
-        const float R1 = fmaf(3.f, t[3], fmaf(2.f, t[2], t[1]));
-        const float R2 = fmaf(9.f, t[3], fmaf(4.f, t[2], t[1]));
-        const float rw = mk.roww[v];
-        M0 = fmaf(rw, R0, M0);
-        Mu = fmaf(rw, R1, Mu);
-        Muu = fmaf(rw, R2, Muu);
-        if (v > 0) {
-          const float fv = (float)v;
-          Mv = fmaf(rw * fv, R0, Mv);
-          Muv = fmaf(rw * fv, R1, Muv);
-          Mvv = fmaf(rw * fv * fv, R0, Mvv);
-        }
-        E += Gv;
-        Gv += two_c;
-        Du += r.cb;
-      }
+      const float M0 = (R0[0] + R0[1]) + (R0[2] + R0[3]);
+      const float Mu = (R1[0] + R1[1]) + (R1[2] + R1[3]);
+      const float Muu = (R2[0] + R2[1]) + (R2[2] + R2[3]);
+      const float Mv = fmaf(3.f, R0[3], fmaf(2.f, R0[2], R0[1]));
+      const float Muv = fmaf(3.f, R1[3], fmaf(2.f, R1[2], R1[1]));
+      const float Mvv = fmaf(9.f, R0[3], fmaf(4.f, R0[2], R0[1]));
       // shift to moments about the Gaussian centre (dx = dx0 + u, dy = dy0 + v), times w
       const float w = r.w;
       float* o = myres + (size_t)i * 6;
@@ -427,7 +578,7 @@ static dim3 render_grid(const gs_config& cfg, int B) {
 }
 
 static size_t render_fwd_smem(const gs_config& cfg) {
-  return sizeof(gs_record) * cfg.chunk + sizeof(uint16_t) * render_warps(cfg.tile) * cfg.chunk;
+  return sizeof(gs_record) * cfg.chunk + sizeof(uint16_t) * (1 + render_warps(cfg.tile)) * cfg.chunk;
 }
 
 static size_t render_bwd_smem(int tile, int chunk) {
