@@ -18,3 +18,4 @@ Parity pins: every function here is pinned by a ``-m "not gpu"`` test in
 quadrature, brute force, library routines for special cases, invariants).
 """
 from .gs_oracle import *  # noqa: F401,F403
+from . import warm_oracle  # noqa: F401,E402  (learned warm start; not in the paper)
