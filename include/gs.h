@@ -220,6 +220,93 @@ int gs_bin_sort_noalloc(const gs_config* cfg, const gs_record* proj, int B, int 
                         uint32_t* pair_gauss, size_t pair_capacity, uint32_t* tile_ranges,
                         uint32_t* n_pairs, gs_stream_t stream, size_t* scratch_needed);
 
+/* -------------------------------------------------------------------------------------
+ * Learned warm start (not in the paper)
+ *
+ * The paper starts every reconstruction from random Gaussians (Sec. 4.1).  These calls
+ * build a learned initializer on top of the method: a coarse backprojection of the
+ * particle images, seeds drawn from it, a point-MLP that maps each seed's neighbourhood to
+ * one Gaussian, and the labels it is trained on (nearest Gaussian of a GMM fitted by the
+ * plain method).  Device pointers, caller-owned, stream-ordered like the rest of the ABI.
+ * ------------------------------------------------------------------------------------- */
+
+/* gs_backproject: vol[Dv][Dv][Dv] ([z][y][x]; voxel centres -E + (idx + 1/2) 2E/Dv) =
+ * mean over the B particles of images[B][D][D] averaged over an f x f stencil of
+ * bilinear samples (one pixel apart, f = max(1, D / Dv)) centred where the voxel centre r
+ * projects: (column, row) = ((W r)_x / h + floor(D/2), floor(D/2) - (W r)_y / h), the
+ * inverse of the pixel centres of App. A.2 Eq. 13.  Outside the image reads zero.  W is
+ * [B][9] row-major (Sec. 3.3.2 Eq. 6).  Passing CTF-multiplied images (gs_apply_ctf) makes
+ * this the adjoint of the coarse image formation model.  1 <= Dv <= 256. */
+int gs_backproject(const float* images, const float* W, int B, int D, float E, int Dv, float* vol,
+                   gs_stream_t stream);
+
+/* gs_mass_estimate: *mass (device float) = h^2 sum_b (-w_b S_b) / sum_b w_b^2, S_b the pixel
+ * sum of image b and w_b = ctf[b][3]: the least-squares total amplitude sum_i A_i, since
+ * the CTF's DC term is -w (App. A.2 Eq. 14) and a splat inside the box integrates to its
+ * amplitude (Eq. 12).  scratch: device double[2].  B >= 1. */
+int gs_mass_estimate(const float* images, const float* ctf, int B, int D, float E, double* scratch, float* mass,
+                     gs_stream_t stream);
+
+/* gs_seed_sample: K seeds drawn from vol[Dv^3] with probability proportional to the integer
+ * weights q_v = floor(fl32(max(vol_v, 0) / vmax) * 2^20) (all 1 if vmax <= 0).  Seed k with
+ * uniforms u[k][0..3] in [0, 1) takes the first voxel whose running weight sum exceeds
+ * t = min(floor(u0 T), T - 1) (T the total, product in FP64) and the point
+ * (-E + (idx + 1/2) dv) + (u_{1,2,3} - 1/2) dv of it, dv = fl32(2E / Dv), each FP32
+ * operation rounded in that order.  Outputs: cdf[Dv^3] (running sums, scratch),
+ * *vmax (device float), voxel[K] (may be NULL), pos[K][3].  The volume must be finite. */
+int gs_seed_sample(const float* vol, int Dv, float E, const float* u, int K, unsigned long long* cdf, float* vmax,
+                   int* voxel, float* pos, gs_stream_t stream);
+
+/* gs_seed_features: feats[K][32] = the volume (trilinear, voxel centres at integer
+ * coordinates, zero outside) at pos + {-1, 0, 1}^3 voxels divided by *vmax (27 values,
+ * z slowest, x fastest), then pos / E (3), then 0, 0. */
+int gs_seed_features(const float* vol, int Dv, float E, const float* vmax, const float* pos, int K, float* feats,
+                     gs_stream_t stream);
+
+/* gs_merge_labels: labels[K][10] of the seeds pos[K][3] against a fitted GMM theta_fit[N][11]:
+ * a mass-preserving coarse-graining of the fitted mixture onto the seeds.  Each fitted
+ * Gaussian g goes to its nearest seed (squared distance ((dx dx + dy dy) + dz dz) in FP32,
+ * each step rounded, ties to the lower seed index) -> assign[N] (int32).  Seed k is the
+ * moment-matched merge of its Gaussians (FP64 sums in moments[K][10], caller scratch):
+ * mass A_k, offset delta_k from the seed, covariance C_k (Sigma = R S S^T R^T, Sec. 3.3.1
+ * Eq. 5, plus the spread of the centres).  Label: delta_k / dv (3); log L00, log L11,
+ * log L22 (clamped to [-6, 3]), L10, L20, L21 of the Cholesky factor of C_k / dv^2 (6);
+ * A_k K / M clamped to [0, 100] (1), M = *mass.  A seed with no Gaussian is labelled
+ * (0, 0, 0, log 1/2 x 3, 0, 0, 0, 0).  dv = 2E / Dv.  K >= 1. */
+int gs_merge_labels(const float* pos, int K, const float* theta_fit, int N, int Dv, float E, const float* mass,
+                    int* assign, double* moments, float* labels, gs_stream_t stream);
+
+/* gs_decode_seeds: raw theta[K][11] from seeds pos[K][3] and pred[K][10] in the label
+ * encoding of gs_merge_labels: mu = pos + dv pred[0..2]; Sigma = dv^2 L L^T; its
+ * eigen-decomposition (cyclic Jacobi, FP64) gives s = softplus^-1(sqrt(lambda)) and q, the
+ * quaternion (w, x, y, z) of the eigenvector matrix with det +1; A = softplus^-1(M / K
+ * max(pred[9], 1e-3)). */
+int gs_decode_seeds(const float* pos, const float* pred, int K, int Dv, float E, const float* mass, float* theta,
+                    gs_stream_t stream);
+
+/* Point-MLP: Z1 = X W1^T + b1, H1 = relu(Z1), Z2 = H1 W2^T + b2, H2 = relu(Z2),
+ * Y = H2 W3^T + b3, widths din, hidden, dout in [1, 128].  Every product rounds both
+ * operands to bfloat16 (nearest even) and accumulates in FP32; biases, activations and
+ * gradients are FP32.  params (FP32, flat): W1[hidden][din], b1[hidden],
+ * W2[hidden][hidden], b2[hidden], W3[dout][hidden], b3[dout]; gs_mlp_param_count gives the
+ * length (host size_t).  Rows of X are X[idx[s]] when idx (int32[n]) is given, else X[s]. */
+int gs_mlp_param_count(int din, int hidden, int dout, size_t* count);
+
+/* acts: n * 4 * hidden floats (Z1, H1, Z2, H2, each [n][hidden]), kept for the backward.
+ * Y: [n][dout]. */
+int gs_mlp_forward(const float* params, int din, int hidden, int dout, const float* X, const int* idx, int n,
+                   float* acts, float* Y, gs_stream_t stream);
+
+/* dparams += dL/dparams for upstream dY[n][dout] (the caller zeroes dparams); the
+ * bfloat16 rounding is passed straight through.  scratch: n * 2 * hidden floats. */
+int gs_mlp_backward(const float* params, int din, int hidden, int dout, const float* X, const int* idx, int n,
+                    const float* acts, const float* dY, float* dparams, float* scratch, gs_stream_t stream);
+
+/* loss[0] += scale * sum (Y[s][c] - T[row(s)][c])^2 and dY = 2 scale (Y - T[row]) (dY may
+ * be NULL); row(s) = idx[s] if idx is given.  scale = 1 / (n width) gives the mean. */
+int gs_mse(const float* Y, const float* T, const int* idx, int n, int width, float scale, float* loss, float* dY,
+           gs_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,17 +31,22 @@ Pieces, in the order the pipeline uses them:
 * ``seed_features``: 32 inputs per seed: the volume at the 27 points seed + {-1, 0, 1}^3
   voxels (trilinear interpolation of the voxel-centre samples, zero outside) divided by
   vmax, then pos / E, then two zeros.
-* ``match_targets``: the label of each seed, from a fitted GMM Theta_fit.  The seed takes
-  the Gaussian g whose centre is nearest (squared distance in FP32,
-  ((dx dx + dy dy) + dz dz) with dx = mu_x - p_x, each step rounded; ties to the lower
-  index) and encodes it in 10 numbers: (mu_g - pos) / dv (3); the log-Cholesky factor of
-  Sigma_g / dv^2 (Sigma = R S S^T R^T, Sec. 3.3.1 Eq. 5): log L00, log L11, log L22, L10,
-  L20, L21 (6); log(A_g K / M) (1).  Log-diagonals are clamped to [-6, 3] and the
-  amplitude log to [-10, 10].
+* ``merge_labels``: the label of each seed, from a fitted GMM Theta_fit: a mass-preserving
+  coarse-graining of the fitted mixture onto the seeds.  Every fitted Gaussian g goes to
+  its nearest seed k(g) (squared distance in FP32, ((dx dx + dy dy) + dz dz) with
+  dx = mu_x - p_x, each step rounded; ties to the lower seed index).  Seed k then stands
+  for the moment-matched merge of its Gaussians: mass A_k = sum A_g, offset
+  delta_k = sum A_g (mu_g - p_k) / A_k and covariance
+  C_k = sum A_g (Sigma_g + (mu_g - p_k)(mu_g - p_k)^T) / A_k - delta_k delta_k^T
+  (Sigma = R S S^T R^T, Sec. 3.3.1 Eq. 5), all in FP64.  Its 10 numbers are delta_k / dv
+  (3); the log-Cholesky factor of C_k / dv^2: log L00, log L11, log L22 clamped to
+  [-6, 3], then L10, L20, L21 (6); the relative mass a_k = A_k K / M clamped to
+  [0, 100] (1).  A seed that receives no Gaussian is labelled (0, 0, 0, log 1/2 x 3,
+  0, 0, 0, 0): no offset, isotropic scale dv / 2, no mass.
 * ``decode``: the inverse map from 10 predicted numbers to raw Theta[K, 11]: mu = pos +
   dv P[0:3]; Sigma = dv^2 L L^T; its eigen-decomposition Sigma = V diag(lambda) V^T with
   det V = +1 gives s = softplus^-1(sqrt(lambda)) and q = quaternion of V (the inverse of
-  Sec. 3.3.1's R(q)); A = softplus^-1(M / K exp(P[9])).
+  Sec. 3.3.1's R(q)); A = softplus^-1(M / K max(P[9], 1e-3)).
 * The point-MLP: three layers, ReLU after the first two, params flat as
   W1[H][din], b1[H], W2[H][H], b2[H], W3[dout][H], b3[dout].  With ``bf16`` every product
   takes both operands rounded to bfloat16 (round to nearest even of the FP32 value) and
@@ -308,29 +313,55 @@ def cholesky3(S):
     return L
 
 
-def encode(pos, theta_g, Dv, mass, K, E=0.5):
-    """Labels[K, 10] of seeds ``pos`` for their matched Gaussians ``theta_g`` (one row each)."""
-    dv = 2.0 * E / Dv
-    theta_g = np.asarray(theta_g, dtype=F64)
-    t = np.zeros((theta_g.shape[0], 10), dtype=F64)
-    t[:, 0:3] = (theta_g[:, 0:3] - np.asarray(pos, dtype=F64)) / dv
-    L = cholesky3(gaussian_covariance(theta_g) / (dv * dv))
-    t[:, 3] = np.clip(np.log(L[:, 0, 0]), -6.0, 3.0)
-    t[:, 4] = np.clip(np.log(L[:, 1, 1]), -6.0, 3.0)
-    t[:, 5] = np.clip(np.log(L[:, 2, 2]), -6.0, 3.0)
-    t[:, 6] = L[:, 1, 0]
-    t[:, 7] = L[:, 2, 0]
-    t[:, 8] = L[:, 2, 1]
-    t[:, 9] = np.clip(np.log(softplus(theta_g[:, 10]) * K / mass), -10.0, 10.0)
-    return t
+EMPTY_LABEL = (0.0, 0.0, 0.0, float(np.log(0.5)), float(np.log(0.5)), float(np.log(0.5)), 0.0, 0.0, 0.0, 0.0)
 
 
-def match_targets(pos, theta_fit, Dv, mass, E=0.5):
-    """(index of the matched Gaussian [K], labels [K, 10])."""
+def merge_moments(pos, theta_fit):
+    """(assignment k(g) [N], mass [K], offset [K, 3], covariance [K, 3, 3]) of the
+    coarse-graining onto the seeds (FP64; empty seeds have mass 0 and zero moments)."""
+    pos = np.asarray(pos, dtype=F32)
     theta_fit = np.asarray(theta_fit, dtype=F32)
-    g = nearest(pos, theta_fit[:, 0:3])
+    K = pos.shape[0]
+    k_of = nearest(theta_fit[:, 0:3], pos)
+    A = softplus(theta_fit[:, 10].astype(F64))
+    d = theta_fit[:, 0:3].astype(F64) - pos[k_of].astype(F64)
+    Sig = gaussian_covariance(theta_fit)
+    mass = np.zeros(K)
+    first = np.zeros((K, 3))
+    second = np.zeros((K, 3, 3))
+    for g in range(theta_fit.shape[0]):
+        k = k_of[g]
+        mass[k] += A[g]
+        first[k] += A[g] * d[g]
+        second[k] += A[g] * (Sig[g] + np.outer(d[g], d[g]))
+    offset = np.zeros((K, 3))
+    cov = np.zeros((K, 3, 3))
+    ok = mass > 0
+    offset[ok] = first[ok] / mass[ok, None]
+    cov[ok] = second[ok] / mass[ok, None, None] - np.einsum("ki,kj->kij", offset[ok], offset[ok])
+    return k_of, mass, offset, cov
+
+
+def merge_labels(pos, theta_fit, Dv, mass_total, E=0.5):
+    """Labels[K, 10] of seeds ``pos`` against the fitted GMM ``theta_fit`` (module docstring)."""
+    dv = 2.0 * E / Dv
     K = np.asarray(pos).shape[0]
-    return g, encode(pos, theta_fit[g].astype(F64), Dv, mass, K, E)
+    _, m, off, C = merge_moments(pos, theta_fit)
+    lab = np.tile(np.asarray(EMPTY_LABEL), (K, 1))
+    ok = m > 0
+    if ok.any():
+        L = cholesky3(C[ok] / (dv * dv))
+        t = np.zeros((int(ok.sum()), 10))
+        t[:, 0:3] = off[ok] / dv
+        t[:, 3] = np.clip(np.log(L[:, 0, 0]), -6.0, 3.0)
+        t[:, 4] = np.clip(np.log(L[:, 1, 1]), -6.0, 3.0)
+        t[:, 5] = np.clip(np.log(L[:, 2, 2]), -6.0, 3.0)
+        t[:, 6] = L[:, 1, 0]
+        t[:, 7] = L[:, 2, 0]
+        t[:, 8] = L[:, 2, 1]
+        t[:, 9] = np.clip(m[ok] * K / mass_total, 0.0, 100.0)
+        lab[ok] = t
+    return lab
 
 
 def decode(pos, pred, Dv, mass, E=0.5):
@@ -356,7 +387,7 @@ def decode(pos, pred, Dv, mass, E=0.5):
     xyzw = Rotation.from_matrix(V).as_quat()  # scalar last
     th[:, 6] = xyzw[:, 3]
     th[:, 7:10] = xyzw[:, 0:3]
-    th[:, 10] = inv_softplus(mass / K * np.exp(np.clip(P[:, 9], -10.0, 10.0)))
+    th[:, 10] = inv_softplus(mass / K * np.maximum(P[:, 9], 1e-3))
     return th
 
 

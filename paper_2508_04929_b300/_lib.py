@@ -67,6 +67,16 @@ _SIGS = {
     "gs_step": [_P, _P, _P, _P, _I, _I, _F, _F, _F, _F, _P],
     "gs_step_counted": [_P, _P, _P, _P, _I, _P, _F, _F, _F, _F, _P],
     "gs_bin_sort_noalloc": [_CFG, _P, _I, _I, _P, _S, _P, _P, _P, ctypes.POINTER(_S)],
+    "gs_backproject": [_P, _P, _I, _I, _F, _I, _P, _P],
+    "gs_mass_estimate": [_P, _P, _I, _I, _F, _P, _P, _P],
+    "gs_seed_sample": [_P, _I, _F, _P, _I, _P, _P, _P, _P, _P],
+    "gs_seed_features": [_P, _I, _F, _P, _P, _I, _P, _P],
+    "gs_merge_labels": [_P, _I, _P, _I, _I, _F, _P, _P, _P, _P, _P],
+    "gs_decode_seeds": [_P, _P, _I, _I, _F, _P, _P, _P],
+    "gs_mlp_param_count": [_I, _I, _I, ctypes.POINTER(_S)],
+    "gs_mlp_forward": [_P, _I, _I, _I, _P, _P, _I, _P, _P, _P],
+    "gs_mlp_backward": [_P, _I, _I, _I, _P, _P, _I, _P, _P, _P, _P, _P],
+    "gs_mse": [_P, _P, _P, _I, _I, _F, _P, _P, _P],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(lib, _name)
@@ -183,3 +193,72 @@ def gs_bin_sort_noalloc(cfg, proj, B, N, pair_gauss, tile_ranges, n_pairs, strea
                                                           _ptr(tile_ranges), _ptr(n_pairs), _stream(stream),
                                                           ctypes.byref(need)))
     return need.value
+
+
+# ---------------------------------------------------------------------------------------
+# Learned warm start
+# ---------------------------------------------------------------------------------------
+def gs_backproject(images, W, Dv, vol, E=0.5, stream=None) -> None:
+    B, D = images.shape[0], images.shape[-1]
+    _check("gs_backproject", lib.gs_backproject(_ptr(images), _ptr(W), B, D, float(E), int(Dv), _ptr(vol),
+                                                _stream(stream)))
+
+
+def gs_mass_estimate(images, ctf, scratch, mass, E=0.5, stream=None) -> None:
+    B, D = images.shape[0], images.shape[-1]
+    _check("gs_mass_estimate", lib.gs_mass_estimate(_ptr(images), _ptr(ctf), B, D, float(E), _ptr(scratch),
+                                                    _ptr(mass), _stream(stream)))
+
+
+def gs_seed_sample(vol, u, cdf, vmax, pos, voxel=None, E=0.5, stream=None) -> None:
+    Dv, K = vol.shape[-1], u.shape[0]
+    _check("gs_seed_sample", lib.gs_seed_sample(_ptr(vol), Dv, float(E), _ptr(u), K, _ptr(cdf), _ptr(vmax),
+                                                _ptr(voxel), _ptr(pos), _stream(stream)))
+
+
+def gs_seed_features(vol, vmax, pos, feats, E=0.5, stream=None) -> None:
+    Dv, K = vol.shape[-1], pos.shape[0]
+    _check("gs_seed_features", lib.gs_seed_features(_ptr(vol), Dv, float(E), _ptr(vmax), _ptr(pos), K,
+                                                    _ptr(feats), _stream(stream)))
+
+
+def gs_merge_labels(pos, theta_fit, Dv, mass, labels, assign=None, moments=None, E=0.5, stream=None) -> None:
+    K, N = pos.shape[0], theta_fit.shape[0]
+    if assign is None:
+        assign = torch.empty(max(N, 1), dtype=torch.int32, device=pos.device)
+    if moments is None:
+        moments = torch.empty(K * 10, dtype=torch.float64, device=pos.device)
+    _check("gs_merge_labels", lib.gs_merge_labels(_ptr(pos), K, _ptr(theta_fit), N, int(Dv), float(E), _ptr(mass),
+                                                  _ptr(assign), _ptr(moments), _ptr(labels), _stream(stream)))
+
+
+def gs_decode_seeds(pos, pred, Dv, mass, theta, E=0.5, stream=None) -> None:
+    _check("gs_decode_seeds", lib.gs_decode_seeds(_ptr(pos), _ptr(pred), pos.shape[0], int(Dv), float(E),
+                                                  _ptr(mass), _ptr(theta), _stream(stream)))
+
+
+def gs_mlp_param_count(din, hidden, dout) -> int:
+    n = _S()
+    _check("gs_mlp_param_count", lib.gs_mlp_param_count(int(din), int(hidden), int(dout), ctypes.byref(n)))
+    return n.value
+
+
+def gs_mlp_forward(params, dims, X, acts, Y, idx=None, stream=None) -> None:
+    din, hidden, dout = dims
+    n = Y.shape[0]
+    _check("gs_mlp_forward", lib.gs_mlp_forward(_ptr(params), din, hidden, dout, _ptr(X), _ptr(idx), n, _ptr(acts),
+                                                _ptr(Y), _stream(stream)))
+
+
+def gs_mlp_backward(params, dims, X, acts, dY, dparams, scratch, idx=None, stream=None) -> None:
+    din, hidden, dout = dims
+    n = dY.shape[0]
+    _check("gs_mlp_backward", lib.gs_mlp_backward(_ptr(params), din, hidden, dout, _ptr(X), _ptr(idx), n,
+                                                  _ptr(acts), _ptr(dY), _ptr(dparams), _ptr(scratch),
+                                                  _stream(stream)))
+
+
+def gs_mse(Y, T, loss, dY=None, idx=None, scale=None, stream=None) -> None:
+    n, width = Y.shape
+    sc = 1.0 / max(n * width, 1) if scale is None else float(scale)
+    _check("gs_mse", lib.gs_mse(_ptr(Y), _ptr(T), _ptr(idx), n, width, sc, _ptr(loss), _ptr(dY), _stream(stream)))

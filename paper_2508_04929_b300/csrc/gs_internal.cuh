@@ -93,6 +93,20 @@ inline cudaError_t ensure_smem(const void* func, size_t bytes, int* cache /* [64
   return e;
 }
 
+// Multiprocessor count of the current device (cached per device): grid sizes of the
+// persistent kernels are multiples of it.
+inline int num_sms() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  if (cache[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+
 // Host-side launchers (one per translation unit).
 cudaError_t launch_activate(const float* theta, int N, float* gauss, float* gacc, int* status, cudaStream_t s);
 cudaError_t launch_project(const gs_config& cfg, const float* gauss, int N, const float* W, int B,

@@ -23,6 +23,7 @@ class Splatter:
     def __init__(self, D, N, B, tile=16, chunk=128, E=0.5, cutoff_sigma=3.0, reduction=0,
                  pair_capacity=None, device="cuda", with_ctf=True):
         self.D, self.N, self.B = int(D), int(N), int(B)
+        self.N_cap = self.N  # buffers hold up to N_cap Gaussians; project() sets the active N
         self.cfg = L.config(D, E, tile, chunk, cutoff_sigma, reduction)
         self.device = torch.device(device)
         self.Tn = L.gs_tiles_per_image(self.cfg)
@@ -57,6 +58,10 @@ class Splatter:
 
     # -- individual steps ------------------------------------------------------------------
     def project(self, theta, W):
+        n = theta.shape[0]
+        if n > self.N_cap or W.shape[0] != self.B:
+            raise ValueError(f"Splatter holds N <= {self.N_cap}, B = {self.B}; got N = {n}, B = {W.shape[0]}")
+        self.N = n
         L.gs_project(self.cfg, theta, W, self.proj, self.ws)
 
     def bin_sort(self, grow=True):

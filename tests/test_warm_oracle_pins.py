@@ -4,8 +4,9 @@ Each function of ``oracle.warm_oracle`` is checked against something other than 
 torch's own bfloat16 conversion and linear layers, central finite differences, exact
 integer arithmetic, closed forms of bilinear and trilinear interpolation on linear fields,
 mass conservation of rendered splats, library routines (numpy searchsorted and Cholesky,
-SciPy's k-d tree), statistics of the sampler, and the encode / decode round trip read back
-through the splatting oracle's own Gaussian builder.
+SciPy's k-d tree), statistics of the sampler, closed forms and invariants of moment
+matching, and the label / decode round trip read back through the splatting oracle's own
+Gaussian builder.
 """
 import numpy as np
 import pytest
@@ -225,32 +226,87 @@ def test_cholesky3_matches_numpy():
     assert np.allclose(WO.cholesky3(S), np.linalg.cholesky(S), atol=1e-13)
 
 
-def test_encode_decode_round_trip_rebuilds_the_gaussians():
-    """decode(encode(theta)) describes the same Gaussians: centres, covariances (read
-    back by the splatting oracle's BuildGaussians, Sec. 3.3.1) and amplitudes."""
+def _separated_gmm(rng, K, D=128):
+    """K Gaussians whose centres are at least 0.05 apart, and seeds within 1e-3 of them
+    (so every Gaussian's nearest seed is its own)."""
+    th = synth.random_gaussians(4 * K, D, rng).astype(F64)
+    keep = []
+    for i in range(th.shape[0]):
+        if all(np.linalg.norm(th[i, 0:3] - th[j, 0:3]) > 0.05 for j in keep):
+            keep.append(i)
+        if len(keep) == K:
+            break
+    th = th[keep]
+    pos = (th[:, 0:3] + rng.uniform(-1e-3, 1e-3, (len(keep), 3))).astype(F32)
+    return th, pos
+
+
+def test_merge_of_one_gaussian_per_seed_round_trips():
+    """With one Gaussian per seed the merge is that Gaussian, and decode(label) rebuilds
+    it: centres, covariances (read back by the splatting oracle's BuildGaussians,
+    Sec. 3.3.1) and amplitudes."""
     rng = synth.rng_for(12)
-    Dv, E, K = 32, 0.5, 64
-    th = synth.random_gaussians(K, 128, rng).astype(F64)
-    pos = th[:, 0:3] + rng.uniform(-0.01, 0.01, (K, 3))
+    Dv, E = 32, 0.5
+    th, pos = _separated_gmm(rng, 40)
+    K = pos.shape[0]
     mass = 3.7
-    lab = WO.encode(pos, th, Dv, mass, K, E)
+    lab = WO.merge_labels(pos, th, Dv, mass, E)
     back = WO.decode(pos, lab, Dv, mass, E)
     g0, g1 = O.build_gaussians(th), O.build_gaussians(back)
     assert np.allclose(g1["mu"], g0["mu"], atol=1e-14)
     assert np.allclose(g1["Sigma"], g0["Sigma"], rtol=1e-9, atol=1e-16)
     assert np.allclose(g1["A"], g0["A"], rtol=1e-12)
-    # the decoded quaternion is a proper rotation of the eigenvectors
+    assert np.allclose(lab[:, 9], g0["A"] * K / mass, rtol=1e-12)
     Rm = O.quat_to_rot(back[:, 6:10] / np.linalg.norm(back[:, 6:10], axis=1, keepdims=True))
     assert np.allclose(np.linalg.det(Rm), 1.0)
 
 
-def test_match_targets_labels_nearest_gaussian():
-    rng = synth.rng_for(13)
-    th = synth.random_gaussians(40, 64, rng)
-    pos = (th[rng.integers(0, 40, 30), 0:3] + rng.normal(0, 1e-3, (30, 3))).astype(F32)
-    g, lab = WO.match_targets(pos, th, 16, 2.0)
-    assert np.array_equal(g, WO.nearest(pos, th[:, 0:3]))
-    assert np.allclose(lab[:, 0:3], (th[g, 0:3].astype(F64) - pos) * 16, atol=1e-12)
+def test_merge_of_two_gaussians_is_closed_form():
+    """Two equal isotropic Gaussians at p +- a e_x merged onto a seed at p: no offset,
+    covariance sigma^2 I + diag(a^2, 0, 0), mass 2A; a far seed receives nothing and gets
+    the empty label."""
+    Dv, E, a, sig = 16, 0.5, 0.01, 0.004
+    dv = 2 * E / Dv
+    sp_raw = float(synth.inv_softplus(np.array(sig)))
+    A_raw = float(synth.inv_softplus(np.array(0.2)))
+    th = np.array([[a, 0, 0, sp_raw, sp_raw, sp_raw, 1, 0, 0, 0, A_raw],
+                   [-a, 0, 0, sp_raw, sp_raw, sp_raw, 0.6, 0.8, 0, 0, A_raw]])
+    pos = np.array([[0.0, 0.0, 0.0], [0.3, 0.3, 0.3]], dtype=F32)
+    lab = WO.merge_labels(pos, th.astype(F32), Dv, 1.0, E)
+    C = (np.diag([a * a, 0, 0]) + sig * sig * np.eye(3)) / dv ** 2
+    Lc = np.linalg.cholesky(C)
+    assert np.allclose(lab[0, 0:3], 0.0, atol=1e-6)
+    assert np.allclose(lab[0, 3:6], np.log(np.diag(Lc)), atol=1e-5)
+    assert np.allclose(lab[0, 6:9], [Lc[1, 0], Lc[2, 0], Lc[2, 1]], atol=1e-6)
+    assert np.isclose(lab[0, 9], 2 * 0.2 * 2 / 1.0, rtol=1e-6)
+    assert np.array_equal(lab[1], np.asarray(WO.EMPTY_LABEL))
+
+
+def test_merge_preserves_mass_and_first_two_moments():
+    """Moment matching keeps the mixture's total mass, mass-weighted mean and second
+    moment (every fitted Gaussian lands on exactly one seed)."""
+    rng = synth.rng_for(14)
+    th = synth.random_gaussians(300, 64, rng)
+    pos = (rng.uniform(-0.3, 0.3, (50, 3))).astype(F32)
+    k_of, m, off, C = WO.merge_moments(pos, th)
+    A = np.log1p(np.exp(th[:, 10].astype(F64)))
+    mu = th[:, 0:3].astype(F64)
+    Sig = np.stack([_indep_cov(r) for r in th])
+    centre = pos.astype(F64) + off
+    assert np.isclose(m.sum(), A.sum(), rtol=1e-13)
+    assert np.allclose((m[:, None] * centre).sum(0), (A[:, None] * mu).sum(0), atol=1e-13)
+    lhs = np.einsum("k,kij->ij", m, C + np.einsum("ki,kj->kij", centre, centre))
+    rhs = np.einsum("g,gij->ij", A, Sig + np.einsum("gi,gj->gij", mu, mu))
+    assert np.allclose(lhs, rhs, rtol=1e-11, atol=1e-15)
+    assert (m == 0).sum() > 0  # some seeds are empty in this draw
+
+
+def _indep_cov(row):
+    th = np.asarray(row, dtype=F64)
+    s = np.log1p(np.exp(th[3:6]))
+    q = th[6:10] / np.linalg.norm(th[6:10])
+    R = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+    return R @ np.diag(s * s) @ R.T
 
 
 def test_steps_to_reach():
