@@ -40,6 +40,11 @@ SM_COUNT = 148
 EX2_PER_CLK_PER_SM = 32  # measured on B300 by a throughput microbenchmark
 SM_MAX_MHZ = 2032.0
 CTF_SNR = 0.05
+# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) per tile pair of one launch of
+# each render kernel, from the capture summarised in profiles/render_kernels_d256_n100k_b64.md
+# (B = 64; the kernels read each pair's index and record once, so traffic scales with the pair
+# count).  Valid only for the gs_render.cu whose SHA-256 is recorded: otherwise null.
+RENDER_TRAFFIC = {"sha256": None, "bytes_per_pair": {"fwd": None, "bwd": None}}
 
 
 def parse():
@@ -65,6 +70,21 @@ def workload(args):
                         f"log-uniform 0.5-3 px scales, random rotations/poses, defocus 1-3 um)",
             "D": args.D, "N": args.N, "batch": args.B, "seed": 0,
             "l2": "inputs larger than L2 (records and gradient partials ~0.8 GB per step)"}
+
+
+def render_traffic(kind, pairs):
+    """DRAM bytes of one render launch over ``pairs`` tile pairs, or None when the kernel
+    source differs from the profiled one."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2508_04929_b300", "csrc", "gs_render.cu")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    per = RENDER_TRAFFIC["bytes_per_pair"].get(kind)
+    if RENDER_TRAFFIC["sha256"] != sha or per is None:
+        return None
+    return per * pairs
 
 
 def make_inputs(args, seed=0):
@@ -412,7 +432,8 @@ def main():
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": 15 * args.steps,
             "roofline": {"bound": "alu", "kernel": f"k_render_{dom}", "achieved": achieved / 1e9,
-                         "peak": peak_exp / 1e9, "unit": "Gex2/s", "frac": achieved / peak_exp, "traffic": None},
+                         "peak": peak_exp / 1e9, "unit": "Gex2/s", "frac": achieved / peak_exp,
+                         "traffic": render_traffic(dom, n_pairs), "peak_source": "measured ex2 rate x 148 SMs x max SM clock"},
             "fwd_bwd_splat": {"ms_fwd": t_fwd, "ms_bwd": t_bwd, "ms_ctf_one_pass": t_ctf, "alg_evals_per_step": e_alg,
                               "pairs_per_step": n_pairs,
                               "frac_of_sfu_roofline": (2 * e_alg / ((t_fwd + t_bwd) * 1e-3)) / peak_exp},
