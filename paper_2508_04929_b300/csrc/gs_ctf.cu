@@ -6,7 +6,11 @@
 // once per CTA (a few CTAs per image) in FP64.  The phase is reduced modulo 2 exactly (the product alpha_hi * n is
 // split into its rounded value and its exact FMA remainder), so sinpi / cospi see an
 // argument accurate to ~1e-7 even where chi reaches hundreds of radians.
+#include <cooperative_groups.h>
+
 #include "gs_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace gs {
 namespace {
@@ -54,13 +58,20 @@ __global__ void k_ctf_mul(float2* __restrict__ spec, const float* __restrict__ c
   }
 }
 
-__global__ void k_loss(const float* __restrict__ X, const float* __restrict__ Y, int P, float scale,
-                       float* __restrict__ loss, float* __restrict__ dLdX) {
-  const int b = blockIdx.x;
+// Loss of one image per cluster of kLossCtas CTAs: each CTA reduces a strided slice of the
+// pixels, and CTA 0 adds the CTAs' sums, read from their shared memory, in rank order (the
+// result does not depend on scheduling).
+constexpr int kLossCtas = 8;
+
+__global__ void __cluster_dims__(kLossCtas, 1, 1) k_loss(const float* __restrict__ X, const float* __restrict__ Y,
+                                                         int P, float scale, float* __restrict__ loss,
+                                                         float* __restrict__ dLdX) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int b = blockIdx.y, part = (int)cluster.block_rank();
   const float* x = X + (size_t)b * P;
   const float* y = Y + (size_t)b * P;
   float acc = 0.f;
-  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+  for (int p = part * blockDim.x + threadIdx.x; p < P; p += kLossCtas * blockDim.x) {
     const float r = x[p] - y[p];
     acc = fmaf(r, r, acc);
     if (dLdX) dLdX[(size_t)b * P + p] = 2.f * scale * r;
@@ -72,8 +83,15 @@ __global__ void k_loss(const float* __restrict__ X, const float* __restrict__ Y,
   if (threadIdx.x < 32) {
     float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (threadIdx.x == 0) loss[b] = v * scale;
+    if (threadIdx.x == 0) red[0] = v;
   }
+  cluster.sync();
+  if (part == 0 && threadIdx.x == 0) {
+    float v = 0.f;
+    for (int r = 0; r < kLossCtas; ++r) v += *cluster.map_shared_rank(&red[0], r);
+    loss[b] = v * scale;
+  }
+  cluster.sync();  // the other CTAs' shared memory stays alive until it has been read
 }
 
 __global__ void k_adam(float* __restrict__ th, const float* __restrict__ g, float* __restrict__ m,
@@ -141,7 +159,7 @@ cudaError_t launch_loss(const gs_config& cfg, const float* X, const float* Y, in
   if (B <= 0) return cudaSuccess;
   const int P = cfg.D * cfg.D;
   const float scale = cfg.reduction == 1 ? 1.f / (float)P : 1.f;
-  k_loss<<<B, 512, 0, s>>>(X, Y, P, scale, loss, dLdX);
+  k_loss<<<dim3(kLossCtas, B), 256, 0, s>>>(X, Y, P, scale, loss, dLdX);
   return cudaGetLastError();
 }
 
