@@ -28,7 +28,10 @@ long Adam takes to fix a unit mismatch.
 """
 from __future__ import annotations
 
+import argparse
+import json
 import math
+import sys
 import time
 from dataclasses import dataclass
 
@@ -191,11 +194,21 @@ def eval_loss(sp: Splatter, theta, mol: Molecule, eval_idx):
     return tot
 
 
+def eval_schedule(steps, every=25, fine_until=100, fine_every=5):
+    """Evaluation steps: every ``fine_every`` up to ``fine_until``, then every ``every``."""
+    s = set(range(0, min(fine_until, steps) + 1, fine_every)) | set(range(0, steps + 1, every)) | {steps}
+    return sorted(s)
+
+
 def fit(sp: Splatter, theta0, mol: Molecule, steps, lr=1e-3, eval_every=0, eval_idx=None, train_idx=None,
-        seed=0):
+        seed=0, eval_at=None):
     """The plain method: Adam (one learning rate for all parameters, Sec. 4.1) on the
     summed squared error of minibatches of sp.B particles.  Returns (theta, steps, losses)
-    with the evaluation loss recorded every ``eval_every`` steps (and at 0 and the end)."""
+    with the evaluation loss recorded at the steps ``eval_at`` (or every ``eval_every``
+    steps, and at 0 and the end)."""
+    if eval_at is None and eval_every:
+        eval_at = sorted(set(range(0, steps + 1, eval_every)) | {steps})
+    eval_at = set(eval_at or ())
     dev = theta0.device
     theta = theta0.clone()
     dtheta = torch.zeros_like(theta)
@@ -213,7 +226,7 @@ def fit(sp: Splatter, theta0, mol: Molecule, steps, lr=1e-3, eval_every=0, eval_
     B = sp.B
     pos = 0
     for step in range(steps + 1):
-        if eval_every and (step % eval_every == 0 or step == steps):
+        if step in eval_at:
             rec_s.append(step)
             rec_l.append(eval_loss(sp, theta, mol, eval_idx))
         if step == steps:
@@ -379,7 +392,7 @@ def steps_to_target(steps, losses, target):
 
 
 def compare_starts(sp: Splatter, mol: Molecule, net: PointMLP, rng, steps=1500, eval_every=25, lr=3e-3,
-                   n_eval=64):
+                   n_eval=64, eval_at=None):
     """Fits of one molecule from the random init, from bare seeds and from the learned
     start.  The target is 1.01 x the loss the random-init fit converges to, taken as the
     lowest evaluation loss of its run (the fit of a finite particle set overfits after
@@ -397,7 +410,8 @@ def compare_starts(sp: Splatter, mol: Molecule, net: PointMLP, rng, steps=1500, 
         "learned": initial_theta(sp, mol, N, rng, net, idx=train_idx),
     }
     for name, th0 in starts.items():
-        _, s, l = fit(sp, th0, mol, steps, lr=lr, eval_every=eval_every, eval_idx=eval_idx, train_idx=train_idx)
+        _, s, l = fit(sp, th0, mol, steps, lr=lr, eval_every=eval_every, eval_idx=eval_idx, train_idx=train_idx,
+                      eval_at=eval_at)
         out[name] = {"steps": s, "loss": l}
     conv = float(np.min(out["random"]["loss"]))
     target = 1.01 * conv
@@ -406,3 +420,94 @@ def compare_starts(sp: Splatter, mol: Molecule, net: PointMLP, rng, steps=1500, 
     out["target"] = target
     out["converged"] = conv
     return out
+
+
+# --------------------------------------------------------------------------------- experiment
+def _timed(fn):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return out, time.perf_counter() - t0
+
+
+def main(argv=None):
+    """Build the training set from plain fits of simulated molecules, train the network and
+    judge it on held-out molecules; prints one JSON summary line."""
+    ap = argparse.ArgumentParser(description="learned warm start: train and judge")
+    ap.add_argument("--molecules", type=int, default=2000)
+    ap.add_argument("--D", type=int, default=128)
+    ap.add_argument("--n-min", type=int, default=5000)
+    ap.add_argument("--n-max", type=int, default=50000)
+    ap.add_argument("--particles", type=int, default=512)
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--fit-steps", type=int, default=1000)
+    ap.add_argument("--lr", type=float, default=3e-3)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--eval-molecules", type=int, default=8)
+    ap.add_argument("--eval-steps", type=int, default=2000)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--out", default=None, help="write the full result (JSON) here")
+    ap.add_argument("--save-net", default=None, help="write the trained network (npz) here")
+    a = ap.parse_args(argv)
+    dev = "cuda"
+
+    def log(msg):
+        print(msg, file=sys.stderr, flush=True)
+
+    data, t_data = _timed(lambda: build_dataset(a.molecules, D=a.D, N_range=(a.n_min, a.n_max), P=a.particles,
+                                                batch=a.batch, fit_steps=a.fit_steps, lr=a.lr, seed=a.seed,
+                                                device=dev, log=log))
+    log(f"dataset: {data.X.shape[0]} seeds from {a.molecules} molecules in {t_data:.1f}s")
+    net = PointMLP(seed=a.seed, device=dev)
+    (curve, val), t_train = _timed(lambda: train(net, data, epochs=a.epochs, lr=2e-3, seed=a.seed, log=log))
+    log(f"trained {a.epochs} epochs in {t_train:.1f}s, validation mse {val:.4f}")
+    if a.save_net:
+        np.savez(a.save_net, dims=np.asarray(net.dims), params=net.state()["params"])
+    samples = data.X.shape[0]
+    del data
+
+    rng = np.random.default_rng([a.seed, 7919])
+    Ns = np.exp(rng.uniform(math.log(a.n_min), math.log(a.n_max), a.eval_molecules)).astype(int)
+    sp = Splatter(a.D, int(Ns.max()), a.batch, tile=8, chunk=128, device=dev)
+    sched = eval_schedule(a.eval_steps)
+    rows = []
+    for i, N in enumerate(Ns):
+        mrng = np.random.default_rng([a.seed, 104729, i])
+        mol = simulate(sp, int(N), a.particles, mrng, device=dev, seed=10 ** 6 + i)
+        res = compare_starts(sp, mol, net, mrng, steps=a.eval_steps, lr=a.lr, eval_at=sched)
+        tr = torch.arange(0, a.particles - 64, device=dev)
+        _, t_warm = _timed(lambda: initial_theta(sp, mol, int(N), mrng, net, idx=tr))
+        _, t_steps = _timed(lambda: fit(sp, random_theta(int(N), mrng, dev), mol, 100, lr=a.lr, train_idx=tr))
+        row = {"N": int(N), "target": res["target"], "warm_start_ms": 1e3 * t_warm, "adam_step_ms": 10.0 * t_steps}
+        for k in ("random", "seeds", "learned"):
+            row[k] = {"steps_to_target": res[k]["steps_to_target"], "loss0": res[k]["loss"][0],
+                      "best": float(np.min(res[k]["loss"])), "steps": res[k]["steps"], "loss": res[k]["loss"]}
+        rows.append(row)
+        log(f"molecule N={N}: steps to target random {row['random']['steps_to_target']} seeds "
+            f"{row['seeds']['steps_to_target']} learned {row['learned']['steps_to_target']}")
+    sp.close()
+
+    def agg(k):
+        v = [r[k]["steps_to_target"] for r in rows]
+        ok = [x for x in v if x is not None]
+        return {"median": float(np.median(ok)) if ok else None, "reached": len(ok), "of": len(v)}
+
+    summary = {
+        "experiment": "learned warm start", "D": a.D, "molecules": a.molecules, "N_range": [a.n_min, a.n_max],
+        "particles": a.particles, "fit_steps": a.fit_steps, "lr": a.lr, "training_seeds": int(samples),
+        "dataset_s": round(t_data, 1), "train_s": round(t_train, 1), "val_mse": val,
+        "steps_to_target": {k: agg(k) for k in ("random", "seeds", "learned")},
+        "learned_best_below_random_best": sum(r["learned"]["best"] < r["random"]["best"] for r in rows),
+        "warm_start_ms_median": float(np.median([r["warm_start_ms"] for r in rows])),
+        "adam_step_ms_median": float(np.median([r["adam_step_ms"] for r in rows])),
+    }
+    if a.out:
+        with open(a.out, "w") as f:
+            json.dump({"summary": summary, "molecules": rows, "train_curve": curve}, f)
+    print(json.dumps(summary))
+    return summary
+
+
+if __name__ == "__main__":
+    main()
