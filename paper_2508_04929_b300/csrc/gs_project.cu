@@ -2,9 +2,10 @@
 // 8; App. A.2 Eqs. 12-13).
 //
 // k_activate runs once per Gaussian (pose independent): softplus of the scales and the
-// amplitude, quaternion normalization, R(q) and M = R diag(s).  k_project runs once per
-// (particle, Gaussian): mu_dot = W mu, Sigma_tilde = (W M)_{2x3} (W M)_{2x3}^T, the k-sigma
-// support box, and the record consumed by the rasterizer.
+// amplitude, quaternion normalization, R(q) and M = R diag(s).  k_project forms, per
+// (particle, Gaussian), mu_dot = W mu, Sigma_tilde = (W M)_{2x3} (W M)_{2x3}^T, the k-sigma
+// support box and the record consumed by the rasterizer; a thread serves one Gaussian for
+// four particles.
 //
 // The support box is an integer decision.  It is computed with explicitly rounded FP32
 // intrinsics (no FMA contraction) in a fixed order, so that any FP32 implementation of the
@@ -85,11 +86,14 @@ __global__ void k_activate(const float* __restrict__ theta, int N, float* __rest
   if (bad) atomicOr(status, GS_STATUS_NONFINITE);
 }
 
-__global__ void k_project(const float* __restrict__ gauss, int N, const float* __restrict__ Wall, int D,
+constexpr int kProjParticles = 4;  // particles per thread: one load of the Gaussian's row serves them all
+
+__global__ void k_project(const float* __restrict__ gauss, int N, const float* __restrict__ Wall, int B, int D,
                           float inv_h, float kcut, gs_record* __restrict__ proj, int* __restrict__ status) {
-  const int b = blockIdx.y;
-  __shared__ float Ws[9];
-  if (threadIdx.x < 9) Ws[threadIdx.x] = Wall[(size_t)b * 9 + threadIdx.x];
+  const int b0 = blockIdx.y * kProjParticles;
+  __shared__ float Wsh[kProjParticles * 9];
+  if (threadIdx.x < kProjParticles * 9 && b0 + (int)threadIdx.x / 9 < B)
+    Wsh[threadIdx.x] = Wall[(size_t)b0 * 9 + threadIdx.x];
   __syncthreads();
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= N) return;
@@ -102,70 +106,75 @@ __global__ void k_project(const float* __restrict__ gauss, int N, const float* _
       G[4 * k] = v.x; G[4 * k + 1] = v.y; G[4 * k + 2] = v.z; G[4 * k + 3] = v.w;
     }
   }
-  float mux = G[kMu], muy = G[kMu + 1], muz = G[kMu + 2];
+  const float mux = G[kMu], muy = G[kMu + 1], muz = G[kMu + 2];
   float M[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) M[k] = G[kM + k];
-  bool bad = G[kBad] != 0.f;
-
-  // V = W_{2x3} M, Sigma_tilde = V V^T (Eqs. 5, 6, 12)
-  float V[2][3];
+  const bool bad_g = G[kBad] != 0.f;
+  bool any_bad = false;
+  for (int p = 0; p < kProjParticles; ++p) {
+    const int b = b0 + p;
+    if (b >= B) break;
+    const float* Ws = Wsh + 9 * p;
+    bool bad = bad_g;
+    // V = W_{2x3} M, Sigma_tilde = V V^T (Eqs. 5, 6, 12)
+    float V[2][3];
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
+    for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int m = 0; m < 3; ++m)
-      V[a][m] = __fadd_rn(__fadd_rn(__fmul_rn(Ws[3 * a + 0], M[0 + m]), __fmul_rn(Ws[3 * a + 1], M[3 + m])),
-                          __fmul_rn(Ws[3 * a + 2], M[6 + m]));
-  float Sxx = __fadd_rn(__fadd_rn(__fmul_rn(V[0][0], V[0][0]), __fmul_rn(V[0][1], V[0][1])),
-                        __fmul_rn(V[0][2], V[0][2]));
-  float Syy = __fadd_rn(__fadd_rn(__fmul_rn(V[1][0], V[1][0]), __fmul_rn(V[1][1], V[1][1])),
-                        __fmul_rn(V[1][2], V[1][2]));
-  float mx = __fadd_rn(__fadd_rn(__fmul_rn(Ws[0], mux), __fmul_rn(Ws[1], muy)), __fmul_rn(Ws[2], muz));
-  float my = __fadd_rn(__fadd_rn(__fmul_rn(Ws[3], mux), __fmul_rn(Ws[4], muy)), __fmul_rn(Ws[5], muz));
-  float c0 = (float)(D / 2);
-  float cx = __fadd_rn(__fmul_rn(mx, inv_h), c0);
-  float cy = __fsub_rn(c0, __fmul_rn(my, inv_h));
-  float rx = __fmul_rn(kcut, __fmul_rn(__fsqrt_rn(Sxx), inv_h));
-  float ry = __fmul_rn(kcut, __fmul_rn(__fsqrt_rn(Syy), inv_h));
-  bad |= !(isfinite(cx) && isfinite(cy) && isfinite(rx) && isfinite(ry));
+      for (int m = 0; m < 3; ++m)
+        V[a][m] = __fadd_rn(__fadd_rn(__fmul_rn(Ws[3 * a + 0], M[0 + m]), __fmul_rn(Ws[3 * a + 1], M[3 + m])),
+                            __fmul_rn(Ws[3 * a + 2], M[6 + m]));
+    const float Sxx = __fadd_rn(__fadd_rn(__fmul_rn(V[0][0], V[0][0]), __fmul_rn(V[0][1], V[0][1])),
+                                __fmul_rn(V[0][2], V[0][2]));
+    const float Syy = __fadd_rn(__fadd_rn(__fmul_rn(V[1][0], V[1][0]), __fmul_rn(V[1][1], V[1][1])),
+                                __fmul_rn(V[1][2], V[1][2]));
+    const float mx = __fadd_rn(__fadd_rn(__fmul_rn(Ws[0], mux), __fmul_rn(Ws[1], muy)), __fmul_rn(Ws[2], muz));
+    const float my = __fadd_rn(__fadd_rn(__fmul_rn(Ws[3], mux), __fmul_rn(Ws[4], muy)), __fmul_rn(Ws[5], muz));
+    const float c0 = (float)(D / 2);
+    const float cx = __fadd_rn(__fmul_rn(mx, inv_h), c0);
+    const float cy = __fsub_rn(c0, __fmul_rn(my, inv_h));
+    const float rx = __fmul_rn(kcut, __fmul_rn(__fsqrt_rn(Sxx), inv_h));
+    const float ry = __fmul_rn(kcut, __fmul_rn(__fsqrt_rn(Syy), inv_h));
+    bad |= !(isfinite(cx) && isfinite(cy) && isfinite(rx) && isfinite(ry));
 
-  // Value path (free FP32).  det Sigma_tilde by the Schur-complement identity
-  // det(Sigma_tilde) = det(Sigma) * (w_z^T Sigma^-1 w_z), w_z the third row of W:
-  // sqrt(det) = s0 s1 s2 * || (w_z^T M)_m / s_m^2 ||, a sum of squares (no cancellation).
-  float Sxy = V[0][0] * V[1][0] + V[0][1] * V[1][1] + V[0][2] * V[1][2];
-  float t0 = (Ws[6] * M[0] + Ws[7] * M[3] + Ws[8] * M[6]) * G[kInvS2];
-  float t1 = (Ws[6] * M[1] + Ws[7] * M[4] + Ws[8] * M[7]) * G[kInvS2 + 1];
-  float t2 = (Ws[6] * M[2] + Ws[7] * M[5] + Ws[8] * M[8]) * G[kInvS2 + 2];
-  float sqrt_det = G[kSprod] * sqrtf(t0 * t0 + t1 * t1 + t2 * t2);
-  float det = sqrt_det * sqrt_det;
-  float wgt = __fdividef(G[kA] * kInv2Pi, sqrt_det);
-  float k2 = __fdividef(-0.5f * kLog2e, det * inv_h * inv_h);
-  bad |= !(isfinite(wgt) && isfinite(k2) && sqrt_det > 0.f);
+    // Value path (free FP32).  det Sigma_tilde by the Schur-complement identity
+    // det(Sigma_tilde) = det(Sigma) * (w_z^T Sigma^-1 w_z), w_z the third row of W:
+    // sqrt(det) = s0 s1 s2 * || (w_z^T M)_m / s_m^2 ||, a sum of squares (no cancellation).
+    const float Sxy = V[0][0] * V[1][0] + V[0][1] * V[1][1] + V[0][2] * V[1][2];
+    const float t0 = (Ws[6] * M[0] + Ws[7] * M[3] + Ws[8] * M[6]) * G[kInvS2];
+    const float t1 = (Ws[6] * M[1] + Ws[7] * M[4] + Ws[8] * M[7]) * G[kInvS2 + 1];
+    const float t2 = (Ws[6] * M[2] + Ws[7] * M[5] + Ws[8] * M[8]) * G[kInvS2 + 2];
+    const float sqrt_det = G[kSprod] * sqrtf(t0 * t0 + t1 * t1 + t2 * t2);
+    const float det = sqrt_det * sqrt_det;
+    const float wgt = __fdividef(G[kA] * kInv2Pi, sqrt_det);
+    const float k2 = __fdividef(-0.5f * kLog2e, det * inv_h * inv_h);
+    bad |= !(isfinite(wgt) && isfinite(k2) && sqrt_det > 0.f);
 
-  gs_record r;
-  r.cx = cx;
-  r.cy = cy;
-  r.ca = k2 * Syy;
-  r.cb = 2.f * k2 * Sxy;
-  r.cc = k2 * Sxx;
-  r.w = wgt;
-  r.x0 = 1; r.x1 = 0; r.y0 = 1; r.y1 = 0;
-  if (!bad) {
-    float x0f = fmaxf(ceilf(__fsub_rn(cx, rx)), 0.f);
-    float x1f = fminf(floorf(__fadd_rn(cx, rx)), (float)(D - 1));
-    float y0f = fmaxf(ceilf(__fsub_rn(cy, ry)), 0.f);
-    float y1f = fminf(floorf(__fadd_rn(cy, ry)), (float)(D - 1));
-    if (x0f <= x1f && y0f <= y1f) {
-      r.x0 = (int16_t)x0f; r.x1 = (int16_t)x1f; r.y0 = (int16_t)y0f; r.y1 = (int16_t)y1f;
+    gs_record r;
+    r.cx = cx;
+    r.cy = cy;
+    r.ca = k2 * Syy;
+    r.cb = 2.f * k2 * Sxy;
+    r.cc = k2 * Sxx;
+    r.w = wgt;
+    r.x0 = 1; r.x1 = 0; r.y0 = 1; r.y1 = 0;
+    if (!bad) {
+      const float x0f = fmaxf(ceilf(__fsub_rn(cx, rx)), 0.f);
+      const float x1f = fminf(floorf(__fadd_rn(cx, rx)), (float)(D - 1));
+      const float y0f = fmaxf(ceilf(__fsub_rn(cy, ry)), 0.f);
+      const float y1f = fminf(floorf(__fadd_rn(cy, ry)), (float)(D - 1));
+      if (x0f <= x1f && y0f <= y1f) {
+        r.x0 = (int16_t)x0f; r.x1 = (int16_t)x1f; r.y0 = (int16_t)y0f; r.y1 = (int16_t)y1f;
+      }
     }
-  } else {
-    atomicOr(status, GS_STATUS_NONFINITE);
+    any_bad |= bad;
+    float4* dst = reinterpret_cast<float4*>(proj + (size_t)b * N + g);
+    const float4* srcp = reinterpret_cast<const float4*>(&r);
+    dst[0] = srcp[0];
+    dst[1] = srcp[1];
   }
-  size_t idx = (size_t)b * N + g;
-  float4* dst = reinterpret_cast<float4*>(proj + idx);
-  const float4* srcp = reinterpret_cast<const float4*>(&r);
-  dst[0] = srcp[0];
-  dst[1] = srcp[1];
+  if (any_bad) atomicOr(status, GS_STATUS_NONFINITE);
 }
 
 }  // namespace
@@ -179,8 +188,8 @@ cudaError_t launch_activate(const float* theta, int N, float* gauss, float* gacc
 cudaError_t launch_project(const gs_config& cfg, const float* gauss, int N, const float* W, int B,
                            gs_record* proj, int* status, cudaStream_t s) {
   if (N <= 0 || B <= 0) return cudaSuccess;
-  dim3 grid((N + 255) / 256, B);
-  k_project<<<grid, 256, 0, s>>>(gauss, N, W, cfg.D, inv_pixel(cfg), cfg.cutoff_sigma, proj, status);
+  dim3 grid((N + 255) / 256, (B + kProjParticles - 1) / kProjParticles);
+  k_project<<<grid, 256, 0, s>>>(gauss, N, W, B, cfg.D, inv_pixel(cfg), cfg.cutoff_sigma, proj, status);
   return cudaGetLastError();
 }
 
