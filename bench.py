@@ -44,7 +44,9 @@ CTF_SNR = 0.05
 # each render kernel, from the capture summarised in profiles/render_kernels_d256_n100k_b64.md
 # (B = 64; the kernels read each pair's index and record once, so traffic scales with the pair
 # count).  Valid only for the gs_render.cu whose SHA-256 is recorded: otherwise null.
-RENDER_TRAFFIC = {"sha256": None, "bytes_per_pair": {"fwd": None, "bwd": None}}
+RENDER_TRAFFIC = {"sha256": "c581fde2c223b61cd4857b9615f8052fdc78c52e06ac9092ece2bec0fcc48793",
+                  "bytes_per_pair": {"fwd": (306.625280e6 + 16.512768e6) / 25319264,
+                                     "bwd": (320.501248e6 + 2.947840e6) / 25319264}}
 
 
 def parse():
@@ -85,6 +87,17 @@ def render_traffic(kind, pairs):
     if RENDER_TRAFFIC["sha256"] != sha or per is None:
         return None
     return per * pairs
+
+
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The maximum of x over all ranks (x itself without a process group): the job's time
+    is that of its slowest rank."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def make_inputs(args, seed=0):
@@ -354,10 +367,7 @@ def main():
             torch.cuda.synchronize()
             for k in kt:
                 kt[k].append(ev[k][0].elapsed_time(ev[k][1]))
-    if dist is not None:
-        tt = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_total = float(tt.item())
+    ms_total = max_over_ranks(ms_total, dist, dev)
     ms_step = ms_total / args.steps
     value = world * args.B / (ms_step * 1e-3)
     t_fwd = statistics.median(kt["fwd"])
