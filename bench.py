@@ -236,6 +236,47 @@ def run_mixed(args, dev, torch, B=128, steps=10):
 
 
 # ---------------------------------------------------------------------------------------
+# evaluation: GMM voxelization (D^3) and FSC against the ground truth
+# ---------------------------------------------------------------------------------------
+def run_evaluation(args, dev, torch, theta, theta_gt, reps=5):
+    from paper_2508_04929_b300 import volume
+    D = args.D
+    for _ in range(2):
+        v1 = volume.voxelize(theta, D)
+        v2 = volume.voxelize(theta_gt, D)
+        curve = volume.fsc(v1, v2)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    tv, tf = [], []
+    for _ in range(reps):
+        e[0].record()
+        v1 = volume.voxelize(theta, D)
+        e[1].record()
+        curve = volume.fsc(v1, v2)
+        e[2].record()
+        torch.cuda.synchronize()
+        tv.append(e[0].elapsed_time(e[1]))
+        tf.append(e[1].elapsed_time(e[2]))
+    # voxel evaluations: the per-axis 3-sigma boxes of the Gaussians (FP32, as in the kernel)
+    import numpy as np
+    from paper_2508_04929_b300 import synth as _s  # noqa: F401
+    th = theta.detach().cpu().numpy().astype(np.float64)
+    s = np.log1p(np.exp(th[:, 3:6]))
+    q = th[:, 6:10] / np.linalg.norm(th[:, 6:10], axis=1, keepdims=True)
+    w, x, y, z = q.T
+    R = np.stack([np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], -1),
+                  np.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], -1),
+                  np.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1)], -2)
+    half = 3.0 * np.sqrt(np.einsum("nam,nm->na", R * R, s * s)) * D
+    evals = float(np.prod(np.floor(2 * half) + 1, axis=1).sum())
+    tv_m, tf_m = statistics.median(tv), statistics.median(tf)
+    return {"workload": f"voxelize N={theta.shape[0]} Gaussians on {D}^3, FSC of two {D}^3 volumes",
+            "voxelize_ms": tv_m, "fsc_ms": tf_m, "voxel_evals": evals,
+            "voxel_evals_per_s": evals / (tv_m * 1e-3),
+            "fsc_vs_ground_truth_shells_1_4_16_64": [float(curve[i]) for i in (1, 4, 16, 64) if i < curve.numel()]}
+
+
+# ---------------------------------------------------------------------------------------
 # the reference arm: the FP64 oracle on the host cores
 # ---------------------------------------------------------------------------------------
 def run_reference(args, rank):
@@ -411,6 +452,9 @@ def main():
     e2e = world * args.B * args.steps / (time.perf_counter() - s0)
     gs.close()
 
+    # --- evaluation: voxelize the fitted and ground-truth GMMs (D^3) and their FSC ---
+    evaluation = run_evaluation(args, dev, torch, prob.theta, torch.from_numpy(th_gt).to(dev))
+
     # --- mixed batch: four volumes of different D and N in one graph (autotuned each) ---
     mixed = None
     if args.mixed:
@@ -450,6 +494,7 @@ def main():
             "cpu_baseline": cpu, "clocks": clocks, "status": st,
             "autotune": tune,
             "mixed_batch": mixed,
+            "evaluation": evaluation,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

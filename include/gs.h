@@ -307,6 +307,46 @@ int gs_mlp_backward(const float* params, int din, int hidden, int dout, const fl
 int gs_mse(const float* Y, const float* T, const int* idx, int n, int width, float scale, float* loss, float* dY,
            gs_stream_t stream);
 
+/* -------------------------------------------------------------------------------------
+ * Evaluation: GMM voxelization and Fourier shell correlation (the paper judges its GMMs by
+ * FSC of the mixture on a voxel grid, Sec. 4, without giving formulas; these are the
+ * library's own definitions)
+ * ------------------------------------------------------------------------------------- */
+
+/* gs_voxelize: vol[Dv][Dv][Dv] (index [k][i][j]) = sum_g A_g N(r; mu_g, Sigma_g), the
+ * normalized 3-D Gaussian density (Sec. 3.3.1 Eqs. 4-5), at r = ((j - floor(Dv/2)) h,
+ * -(i - floor(Dv/2)) h, (k - floor(Dv/2)) h), h = 2E / Dv: the pixel grid of App. A.2 Eq. 13
+ * extended along z, so that sum_k vol[k] h is the image rendered at W = I.  Gaussian g adds
+ * only inside its per-axis k-sigma box [ceil(c - r), floor(c + r)] (c its centre in voxel
+ * units, r = cutoff_sigma sqrt(Sigma_aa) / h, clipped to the grid), decided in FP32 with
+ * correctly rounded operations in a fixed order: Sigma_aa = ((M_a0^2 + M_a1^2) + M_a2^2) with
+ * M = R diag(s) as in gs_project, r = k (sqrt(Sigma_aa) (1/h)), c_x = mu_x (1/h) + floor(Dv/2),
+ * c_y = floor(Dv/2) - mu_y (1/h), c_z = mu_z (1/h) + floor(Dv/2), 1/h = fl32(Dv / 2E).
+ * Contributions are added with atomics, so the summation order (and the last bits) can vary
+ * between runs.  Gaussians with non-finite parameters are skipped.  ws: workspace of
+ * gs_voxel_workspace_size(N) bytes.  1 <= Dv <= 1024. */
+int gs_voxel_workspace_size(int N, size_t* bytes);
+int gs_voxelize(const float* theta, int N, int Dv, float E, float cutoff_sigma, float* vol, void* ws, size_t ws_bytes,
+                gs_stream_t stream);
+
+/* Fourier shell correlation of two D^3 volumes.  FSC(s) = Re sum F1 conj(F2) /
+ * sqrt(sum |F1|^2 sum |F2|^2) over the coefficients of shell s = 0 .. D/2, the shell of
+ * frequency index (kx, ky, kz) (signed, DFT order) being the integer nearest to |k|.  The
+ * sums run over the R2C half spectrum with Hermitian weights (1 for kx = 0 and kx = D/2,
+ * 2 otherwise) in FP64.  gs_fsc_create makes the cuFFT plan (host call, not stream-ordered);
+ * gs_fsc writes fsc[D/2 + 1] (device) using a workspace of gs_fsc_workspace_size bytes. */
+typedef struct gs_fsc_plan {
+  int r2c;           /* cuFFT handle */
+  int D;
+  size_t work_bytes; /* cuFFT work area (inside the gs_fsc workspace) */
+} gs_fsc_plan;
+
+int gs_fsc_create(int D, gs_fsc_plan* plan);
+int gs_fsc_destroy(gs_fsc_plan* plan);
+int gs_fsc_workspace_size(const gs_fsc_plan* plan, size_t* bytes);
+int gs_fsc(const gs_fsc_plan* plan, const float* vol1, const float* vol2, float* fsc, void* ws, size_t ws_bytes,
+           gs_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

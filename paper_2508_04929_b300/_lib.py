@@ -38,6 +38,10 @@ class GsFFT(ctypes.Structure):
                 ("work_bytes", ctypes.c_size_t)]
 
 
+class GsFSC(ctypes.Structure):
+    _fields_ = [("r2c", ctypes.c_int), ("D", ctypes.c_int), ("work_bytes", ctypes.c_size_t)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise RuntimeError(f"libgs.so not built ({LIB_PATH}); run python -m paper_2508_04929_b300.build")
@@ -77,6 +81,12 @@ _SIGS = {
     "gs_mlp_forward": [_P, _I, _I, _I, _P, _P, _I, _P, _P, _P],
     "gs_mlp_backward": [_P, _I, _I, _I, _P, _P, _I, _P, _P, _P, _P, _P],
     "gs_mse": [_P, _P, _P, _I, _I, _F, _P, _P, _P],
+    "gs_voxel_workspace_size": [_I, ctypes.POINTER(_S)],
+    "gs_voxelize": [_P, _I, _I, _F, _F, _P, _P, _S, _P],
+    "gs_fsc_create": [_I, ctypes.POINTER(GsFSC)],
+    "gs_fsc_destroy": [ctypes.POINTER(GsFSC)],
+    "gs_fsc_workspace_size": [ctypes.POINTER(GsFSC), ctypes.POINTER(_S)],
+    "gs_fsc": [ctypes.POINTER(GsFSC), _P, _P, _P, _P, _S, _P],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(lib, _name)
@@ -262,3 +272,38 @@ def gs_mse(Y, T, loss, dY=None, idx=None, scale=None, stream=None) -> None:
     n, width = Y.shape
     sc = 1.0 / max(n * width, 1) if scale is None else float(scale)
     _check("gs_mse", lib.gs_mse(_ptr(Y), _ptr(T), _ptr(idx), n, width, sc, _ptr(loss), _ptr(dY), _stream(stream)))
+
+
+# ---------------------------------------------------------------------------------------
+# Evaluation: voxelization and FSC
+# ---------------------------------------------------------------------------------------
+def gs_voxel_workspace_size(N) -> int:
+    n = _S()
+    _check("gs_voxel_workspace_size", lib.gs_voxel_workspace_size(int(N), ctypes.byref(n)))
+    return n.value
+
+
+def gs_voxelize(theta, Dv, vol, ws, E=0.5, cutoff_sigma=3.0, stream=None) -> None:
+    _check("gs_voxelize", lib.gs_voxelize(_ptr(theta), theta.shape[0], int(Dv), float(E), float(cutoff_sigma),
+                                          _ptr(vol), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def gs_fsc_create(D) -> GsFSC:
+    f = GsFSC()
+    _check("gs_fsc_create", lib.gs_fsc_create(int(D), ctypes.byref(f)))
+    return f
+
+
+def gs_fsc_destroy(f: GsFSC) -> None:
+    _check("gs_fsc_destroy", lib.gs_fsc_destroy(ctypes.byref(f)))
+
+
+def gs_fsc_workspace_size(f: GsFSC) -> int:
+    n = _S()
+    _check("gs_fsc_workspace_size", lib.gs_fsc_workspace_size(ctypes.byref(f), ctypes.byref(n)))
+    return n.value
+
+
+def gs_fsc(f: GsFSC, vol1, vol2, out, ws, stream=None) -> None:
+    _check("gs_fsc", lib.gs_fsc(ctypes.byref(f), _ptr(vol1), _ptr(vol2), _ptr(out), _ptr(ws),
+                                ws.numel() * ws.element_size(), _stream(stream)))
