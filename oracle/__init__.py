@@ -20,3 +20,4 @@ quadrature, brute force, library routines for special cases, invariants).
 from .gs_oracle import *  # noqa: F401,F403
 from . import warm_oracle  # noqa: F401,E402  (learned warm start; not in the paper)
 from . import volume_oracle  # noqa: F401,E402  (voxelization and FSC)
+from . import pose_oracle  # noqa: F401,E402  (pose and translation gradients)
