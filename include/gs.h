@@ -183,6 +183,20 @@ int gs_render_bwd(const gs_config* cfg, const float* theta, int N, const float* 
                   const gs_record* proj, const uint32_t* pair_gauss, const uint32_t* tile_ranges,
                   const float* dLdQ, float* dtheta, void* ws, size_t ws_bytes, gs_stream_t stream);
 
+/* gs_render_bwd_pose: gs_render_bwd plus the gradients with respect to each particle's pose
+ * and in-plane translation.  The paper keeps poses fixed (Sec. 4.1) and names their joint
+ * optimization as future work (Sec. 5); these follow from the same chain one step earlier:
+ * mu_dot = W mu and Sigma_dot = W Sigma W^T (Eq. 6) give, summed over the particle's
+ * (Gaussian, tile) pairs, dL/dW = grad_mu_dot mu^T + G W Sigma^T + G^T W Sigma with
+ * G = [[grad_Sigma_tilde, 0], [0, 0]] (Eq. 21), and a translation t of the model image
+ * (mu_tilde -> mu_tilde + t, at t = 0) gives dL/dt = sum grad_mu_tilde.
+ * dpose[B * 12] (device, 16-byte aligned) is ACCUMULATED (the caller zeroes it):
+ * dL/dW row-major at 0..8 (row 2 stays 0: depth does not enter the image), 9 unused,
+ * dL/dt at 10..11 (model units).  The summation order of dpose varies between runs. */
+int gs_render_bwd_pose(const gs_config* cfg, const float* theta, int N, const float* W, int B, const gs_record* proj,
+                       const uint32_t* pair_gauss, const uint32_t* tile_ranges, const float* dLdQ, float* dtheta,
+                       float* dpose, void* ws, size_t ws_bytes, gs_stream_t stream);
+
 /* Adam step with one learning rate for all parameters (Sec. 4.1):
  * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; theta -= lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps).
  * t >= 1 counts steps.  n = 11 N. */

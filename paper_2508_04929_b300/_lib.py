@@ -68,6 +68,7 @@ _SIGS = {
     "gs_apply_ctf": [_CFG, _P, _P, _I, _P, ctypes.POINTER(GsFFT), _P, _S, _P],
     "gs_loss": [_CFG, _P, _P, _I, _P, _P, _P],
     "gs_render_bwd": [_CFG, _P, _I, _P, _I, _P, _P, _P, _P, _P, _P, _S, _P],
+    "gs_render_bwd_pose": [_CFG, _P, _I, _P, _I, _P, _P, _P, _P, _P, _P, _P, _S, _P],
     "gs_step": [_P, _P, _P, _P, _I, _I, _F, _F, _F, _F, _P],
     "gs_step_counted": [_P, _P, _P, _P, _I, _P, _F, _F, _F, _F, _P],
     "gs_bin_sort_noalloc": [_CFG, _P, _I, _I, _P, _S, _P, _P, _P, ctypes.POINTER(_S)],
@@ -181,6 +182,15 @@ def gs_render_bwd(cfg, theta, W, proj, pair_gauss, tile_ranges, dLdQ, dtheta, ws
     _check("gs_render_bwd", lib.gs_render_bwd(ctypes.byref(cfg), _ptr(theta), N, _ptr(W), B, _ptr(proj),
                                               _ptr(pair_gauss), _ptr(tile_ranges), _ptr(dLdQ), _ptr(dtheta),
                                               _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def gs_render_bwd_pose(cfg, theta, W, proj, pair_gauss, tile_ranges, dLdQ, dtheta, dpose, ws, stream=None) -> None:
+    """gs_render_bwd plus dL/dW (dpose[:, 0:9]) and dL/dt (dpose[:, 10:12]), accumulated."""
+    N, B = theta.shape[0], W.shape[0]
+    _check("gs_render_bwd_pose", lib.gs_render_bwd_pose(ctypes.byref(cfg), _ptr(theta), N, _ptr(W), B, _ptr(proj),
+                                                        _ptr(pair_gauss), _ptr(tile_ranges), _ptr(dLdQ),
+                                                        _ptr(dtheta), _ptr(dpose), _ptr(ws),
+                                                        ws.numel() * ws.element_size(), _stream(stream)))
 
 
 def gs_step(theta, dtheta, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None) -> None:

@@ -172,20 +172,38 @@ int gs_loss(const gs_config* cfg, const float* X, const float* Y, int B, float* 
   return cuda_rc(launch_loss(*cfg, X, Y, B, loss, dLdX, (cudaStream_t)stream));
 }
 
-int gs_render_bwd(const gs_config* cfg, const float* theta, int N, const float* W, int B, const gs_record* proj,
-                  const uint32_t* pair_gauss, const uint32_t* tile_ranges, const float* dLdQ, float* dtheta,
-                  void* ws, size_t ws_bytes, gs_stream_t stream) {
+static int render_bwd_impl(const gs_config* cfg, const float* theta, int N, const float* W, int B,
+                           const gs_record* proj, const uint32_t* pair_gauss, const uint32_t* tile_ranges,
+                           const float* dLdQ, float* dtheta, float* dpose, void* ws, size_t ws_bytes,
+                           gs_stream_t stream) {
   if (!cfg_ok(cfg) || !sizes_ok(cfg, B, N)) return GS_EINVAL;
   if (!ws || !aligned(ws, 256)) return GS_EINVAL;
   if (N > 0 && (!theta || !dtheta)) return GS_EINVAL;
   if (N > 0 && B > 0 && (!W || !proj || !tile_ranges || !dLdQ || !aligned(proj, 16))) return GS_EINVAL;
+  if (dpose && !aligned(dpose, 16)) return GS_EINVAL;
   const WsLayout L = ws_layout(*cfg, B, N, 0);
   if (ws_bytes < L.spec) return GS_ENOSPC;
   cudaStream_t s = (cudaStream_t)stream;
   float* gacc = ws_ptr<float>(ws, L.gacc);
-  cudaError_t e = launch_render_bwd(*cfg, proj, N, pair_gauss, tile_ranges, B, dLdQ, W, gacc, s);
-  if (e == cudaSuccess) e = launch_bwd_finalize(theta, ws_ptr<float>(ws, L.gauss), N, gacc, dtheta, s);
+  const float* gauss = ws_ptr<float>(ws, L.gauss);
+  cudaError_t e = launch_render_bwd(*cfg, proj, N, pair_gauss, tile_ranges, B, dLdQ, W, gacc, gauss, dpose, s);
+  if (e == cudaSuccess) e = launch_bwd_finalize(theta, gauss, N, gacc, dtheta, s);
   return cuda_rc(e);
+}
+
+int gs_render_bwd(const gs_config* cfg, const float* theta, int N, const float* W, int B, const gs_record* proj,
+                  const uint32_t* pair_gauss, const uint32_t* tile_ranges, const float* dLdQ, float* dtheta,
+                  void* ws, size_t ws_bytes, gs_stream_t stream) {
+  return render_bwd_impl(cfg, theta, N, W, B, proj, pair_gauss, tile_ranges, dLdQ, dtheta, nullptr, ws, ws_bytes,
+                         stream);
+}
+
+int gs_render_bwd_pose(const gs_config* cfg, const float* theta, int N, const float* W, int B, const gs_record* proj,
+                       const uint32_t* pair_gauss, const uint32_t* tile_ranges, const float* dLdQ, float* dtheta,
+                       float* dpose, void* ws, size_t ws_bytes, gs_stream_t stream) {
+  if (B > 0 && !dpose) return GS_EINVAL;
+  return render_bwd_impl(cfg, theta, N, W, B, proj, pair_gauss, tile_ranges, dLdQ, dtheta, dpose, ws, ws_bytes,
+                         stream);
 }
 
 int gs_step(float* theta, const float* dtheta, float* m, float* v, int n, int t, float lr, float beta1,

@@ -124,8 +124,8 @@ cudaError_t launch_render_fwd(const gs_config& cfg, const gs_record* proj, int N
                               const uint32_t* pair_gauss, const uint32_t* ranges, int B, float* Q,
                               cudaStream_t s);
 cudaError_t launch_render_bwd(const gs_config& cfg, const gs_record* proj, int N,
-                              const uint32_t* pair_gauss, const uint32_t* ranges, int B,
-                              const float* dLdQ, const float* W, float* gacc, cudaStream_t s);
+                              const uint32_t* pair_gauss, const uint32_t* ranges, int B, const float* dLdQ,
+                              const float* W, float* wacc, const float* gauss, float* dpose, cudaStream_t s);
 cudaError_t launch_bwd_finalize(const float* theta, const float* gauss, int N, float* gacc, float* dtheta,
                                 cudaStream_t s);
 cudaError_t launch_ctf_mul(const gs_config& cfg, float2* spec, const float* ctf, int B, cudaStream_t s);

@@ -239,8 +239,12 @@ __device__ __forceinline__ void bwd_item(Item& it, const u64 (*g2)[4], const Rec
 
 // World-space gradient of one (particle, Gaussian) pair from its moment sums, added into
 // the Gaussian's accumulator.  W holds the first two rows of the pose.
-__device__ __forceinline__ void flush_grad(const Rec& r, const float S[6], const float W[6], float kap, float h,
-                                           float* __restrict__ dst) {
+struct Grad2 {
+  float gmx, gmy, gxx, gxy, gyy;  // grad_mu_tilde, grad_Sigma_tilde (full-matrix, symmetric)
+};
+
+__device__ __forceinline__ Grad2 flush_grad(const Rec& r, const float S[6], const float W[6], float kap, float h,
+                                            float* __restrict__ dst) {
   const float pxx = kap * r.ca, pyy = kap * r.cc, pxy = -0.5f * kap * r.cb;
   // App. A.2 Eq. 18: grad_mu_tilde = sum Gc P d, d = (h dx, -h dy)
   const float gmx = h * (pxx * S[1] - pxy * S[2]);
@@ -267,6 +271,50 @@ __device__ __forceinline__ void flush_grad(const Rec& r, const float S[6], const
   red_add_v4(dst, o[0], o[1], o[2], o[3]);
   red_add_v4(dst + 4, o[4], o[5], o[6], o[7]);
   red_add_v2(dst + 8, o[8], o[9]);
+  return Grad2{gmx, gmy, gxx, gxy, gyy};
+}
+
+// Pose gradients of one (particle, Gaussian) pair: mu_dot = W mu and Sigma_dot = W Sigma W^T
+// give dL/dW = grad_mu_dot mu^T + 2 G W Sigma (G the embedded grad_Sigma_tilde, symmetric;
+// rows 0 and 1 only), and a model translation t gives dL/dt = grad_mu_tilde.  acc: dW rows
+// 0 and 1 (6 values), dt (2 values).  G row of the activated table: mu, M = R diag(s).
+__device__ __forceinline__ void pose_accum(float acc[8], const float* __restrict__ Grow, const float W[6],
+                                           const Grad2& q) {
+  const float4 a0 = __ldg(reinterpret_cast<const float4*>(Grow));      // mu[3], M00
+  const float4 a1 = __ldg(reinterpret_cast<const float4*>(Grow) + 1);  // M01 M02 M10 M11
+  const float4 a2 = __ldg(reinterpret_cast<const float4*>(Grow) + 2);  // M12 M20 M21 M22
+  const float mu[3] = {a0.x, a0.y, a0.z};
+  const float M[9] = {a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
+  float V[2][3], WS[2][3];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int m = 0; m < 3; ++m) V[a][m] = W[3 * a] * M[m] + W[3 * a + 1] * M[3 + m] + W[3 * a + 2] * M[6 + m];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) WS[a][i] = V[a][0] * M[3 * i] + V[a][1] * M[3 * i + 1] + V[a][2] * M[3 * i + 2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    acc[i] += q.gmx * mu[i] + 2.f * (q.gxx * WS[0][i] + q.gxy * WS[1][i]);
+    acc[3 + i] += q.gmy * mu[i] + 2.f * (q.gxy * WS[0][i] + q.gyy * WS[1][i]);
+  }
+  acc[6] += q.gmx;
+  acc[7] += q.gmy;
+}
+
+// Warp sum of the lanes' pose accumulators, added by lane 0 into dpose[12] (dW row-major,
+// rows 0 and 1 at 0..5; dt at 10 and 11, 8-byte aligned for the vector reduction).
+__device__ __forceinline__ void pose_flush(float acc[8], float* __restrict__ dpose) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+  if ((threadIdx.x & 31) == 0) {
+    red_add_v4(dpose, acc[0], acc[1], acc[2], acc[3]);
+    red_add_v2(dpose + 4, acc[4], acc[5]);
+    red_add_v2(dpose + 10, acc[6], acc[7]);
+  }
 }
 
 // dL/dQ of the block into g2 (shared, [u][rp] packed row pairs); called by one warp.
@@ -325,12 +373,15 @@ __global__ void __launch_bounds__(kTileWarps * 32, kFwd8MinBlocks) k_render_fwd8
   store_block(acc, Q, b, D, X, Y);
 }
 
+template <bool kPose>
 __global__ void __launch_bounds__(kTileWarps * 32) k_render_bwd8(const gs_record* __restrict__ proj, int N,
                                                                  const uint32_t* __restrict__ pair_gauss,
                                                                  const uint32_t* __restrict__ ranges, int D, int ntx,
                                                                  const float* __restrict__ dLdQ,
                                                                  const float* __restrict__ Wall, float h,
-                                                                 float* __restrict__ wacc) {
+                                                                 float* __restrict__ wacc,
+                                                                 const float* __restrict__ gauss,
+                                                                 float* __restrict__ dpose) {
   __shared__ __align__(16) u64 g2all[kTileWarps][kB][4];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, b = blockIdx.y;
   const int tile = blockIdx.x * kTileWarps + warp;
@@ -347,6 +398,7 @@ __global__ void __launch_bounds__(kTileWarps * 32) k_render_bwd8(const gs_record
   const float kap = -2.f / (kLog2e * h * h);  // P = kap * [[ca, -cb/2], [-cb/2, cc]]
   __syncwarp();
   const float4* pr = reinterpret_cast<const float4*>(proj + (size_t)b * N);
+  float pacc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   uint32_t i = start + lane;
   float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na;
   uint32_t g0 = 0, g1 = 0;
@@ -369,8 +421,10 @@ __global__ void __launch_bounds__(kTileWarps * 32) k_render_bwd8(const gs_record
     Item it = make_item(r, X, Y);
     float S[6];
     bwd_item(it, g2, r, X, Y, S);
-    flush_grad(r, S, W, kap, h, wacc + (size_t)g * kGradStride);
+    const Grad2 q = flush_grad(r, S, W, kap, h, wacc + (size_t)g * kGradStride);
+    if (kPose) pose_accum(pacc, gauss + (size_t)g * kGaussStride, W, q);
   }
+  if (kPose) pose_flush(pacc, dpose + (size_t)b * 12);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -473,12 +527,15 @@ __global__ void __launch_bounds__(kRegionWarps * 32) k_render_fwd16(const gs_rec
   store_block(acc, Q, b, D, X, Y);
 }
 
+template <bool kPose>
 __global__ void __launch_bounds__(kRegionWarps * 32) k_render_bwd16(const gs_record* __restrict__ proj, int N,
                                                                     const uint32_t* __restrict__ pair_gauss,
                                                                     const uint32_t* __restrict__ ranges, int D, int T,
                                                                     int ntx, int chunk, const float* __restrict__ dLdQ,
                                                                     const float* __restrict__ Wall, float h,
-                                                                    float* __restrict__ wacc) {
+                                                                    float* __restrict__ wacc,
+                                                                    const float* __restrict__ gauss,
+                                                                    float* __restrict__ dpose) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(16) u64 g2all[kRegionWarps][kB][4];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -499,6 +556,7 @@ __global__ void __launch_bounds__(kRegionWarps * 32) k_render_bwd16(const gs_rec
   for (int c = 0; c < 6; ++c) W[c] = Wall[(size_t)b * 9 + c];
   const float kap = -2.f / (kLog2e * h * h);
   const size_t pbase = (size_t)b * N;
+  float pacc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   for (uint32_t base = start; base < end; base += chunk) {
     const int n = (int)min((uint32_t)chunk, end - base);
     __syncthreads();
@@ -512,9 +570,11 @@ __global__ void __launch_bounds__(kRegionWarps * 32) k_render_bwd16(const gs_rec
       Item it = make_item(r, X, Y);
       float S[6];
       bwd_item(it, g2all[warp], r, X, Y, S);
-      flush_grad(r, S, W, kap, h, wacc + (size_t)gid[k] * kGradStride);
+      const Grad2 q = flush_grad(r, S, W, kap, h, wacc + (size_t)gid[k] * kGradStride);
+      if (kPose) pose_accum(pacc, gauss + (size_t)gid[k] * kGaussStride, W, q);
     }
   }
+  if (kPose) pose_flush(pacc, dpose + (size_t)b * 12);
 }
 
 // Per Gaussian: dL/dA = sum S0 / A and the chain from (grad_mu, grad_Sigma) to theta.
@@ -621,23 +681,33 @@ cudaError_t launch_render_fwd(const gs_config& cfg, const gs_record* proj, int N
 
 cudaError_t launch_render_bwd(const gs_config& cfg, const gs_record* proj, int N, const uint32_t* pair_gauss,
                               const uint32_t* ranges, int B, const float* dLdQ, const float* W, float* wacc,
-                              cudaStream_t s) {
+                              const float* gauss, float* dpose, cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
   const int ntx = (cfg.D + cfg.tile - 1) / cfg.tile;
   const float h = 2.f * cfg.E / (float)cfg.D;
   if (cfg.tile == 8) {
     const dim3 grid((ntx * ntx + kTileWarps - 1) / kTileWarps, B);
-    k_render_bwd8<<<grid, kTileWarps * 32, 0, s>>>(proj, N, pair_gauss, ranges, cfg.D, ntx, dLdQ, W, h, wacc);
+    if (dpose)
+      k_render_bwd8<true><<<grid, kTileWarps * 32, 0, s>>>(proj, N, pair_gauss, ranges, cfg.D, ntx, dLdQ, W, h, wacc,
+                                                            gauss, dpose);
+    else
+      k_render_bwd8<false><<<grid, kTileWarps * 32, 0, s>>>(proj, N, pair_gauss, ranges, cfg.D, ntx, dLdQ, W, h, wacc,
+                                                             gauss, dpose);
     return cudaGetLastError();
   }
   const size_t sm = region_smem(cfg.chunk, true);
   {
-    static int cache[64] = {0};
-    cudaError_t e = ensure_smem((const void*)k_render_bwd16, sm, cache);
+    static int cache[2][64] = {{0}};
+    cudaError_t e = dpose ? ensure_smem((const void*)k_render_bwd16<true>, sm, cache[1])
+                          : ensure_smem((const void*)k_render_bwd16<false>, sm, cache[0]);
     if (e != cudaSuccess) return e;
   }
-  k_render_bwd16<<<render_grid(cfg, B), kRegionWarps * 32, sm, s>>>(proj, N, pair_gauss, ranges, cfg.D, cfg.tile,
-                                                                    ntx, cfg.chunk, dLdQ, W, h, wacc);
+  if (dpose)
+    k_render_bwd16<true><<<render_grid(cfg, B), kRegionWarps * 32, sm, s>>>(
+        proj, N, pair_gauss, ranges, cfg.D, cfg.tile, ntx, cfg.chunk, dLdQ, W, h, wacc, gauss, dpose);
+  else
+    k_render_bwd16<false><<<render_grid(cfg, B), kRegionWarps * 32, sm, s>>>(
+        proj, N, pair_gauss, ranges, cfg.D, cfg.tile, ntx, cfg.chunk, dLdQ, W, h, wacc, gauss, dpose);
   return cudaGetLastError();
 }
 

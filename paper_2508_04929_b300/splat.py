@@ -90,8 +90,13 @@ class Splatter:
         L.gs_loss(self.cfg, X, Y, self.loss, self.dX)
         return self.loss[: self.B], self.dX
 
-    def backward(self, theta, W, dQ, dtheta):
-        L.gs_render_bwd(self.cfg, theta, W, self.proj, self.pairs, self.ranges, dQ, dtheta, self.ws)
+    def backward(self, theta, W, dQ, dtheta, dpose=None):
+        """Accumulates dL/dtheta into dtheta; with ``dpose`` ([B, 12], zeroed by the caller)
+        also dL/dW (dpose[:, 0:9], row-major) and dL/dt (dpose[:, 10:12])."""
+        if dpose is None:
+            L.gs_render_bwd(self.cfg, theta, W, self.proj, self.pairs, self.ranges, dQ, dtheta, self.ws)
+        else:
+            L.gs_render_bwd_pose(self.cfg, theta, W, self.proj, self.pairs, self.ranges, dQ, dtheta, dpose, self.ws)
         return dtheta
 
     def status(self, clear=True) -> int:
