@@ -21,3 +21,4 @@ from .gs_oracle import *  # noqa: F401,F403
 from . import warm_oracle  # noqa: F401,E402  (learned warm start; not in the paper)
 from . import volume_oracle  # noqa: F401,E402  (voxelization and FSC)
 from . import pose_oracle  # noqa: F401,E402  (pose and translation gradients)
+from . import algo_oracle  # noqa: F401,E402  (FourierShift and SplitGaussian of Algorithm 1)
