@@ -361,6 +361,29 @@ int gs_fsc_workspace_size(const gs_fsc_plan* plan, size_t* bytes);
 int gs_fsc(const gs_fsc_plan* plan, const float* vol1, const float* vol2, float* fsc, void* ws, size_t ws_bytes,
            gs_stream_t stream);
 
+/* -------------------------------------------------------------------------------------
+ * The remaining steps of Algorithm 1 (FourierShift, SplitGaussian).  The paper gives no
+ * formula for either; these are the library's definitions.
+ * ------------------------------------------------------------------------------------- */
+
+/* gs_fourier_shift: out[b] = in[b] moved by t[b] = (t_x, t_y) (model units) on the periodic
+ * pixel grid ("center alignment" with the published translations, Algorithm 1, Sec. 4.1):
+ * the R2C spectrum is multiplied by exp(-2 pi i (m s_x + l s_y) / D) with s_x = t_x / h
+ * (columns) and s_y = -t_y / h (rows grow downward, App. A.2 Eq. 13), the factor of each
+ * axis replaced by cos(pi s) at its Nyquist index for even D (so the result stays real and an
+ * integer shift is a circular roll).  fft and ws as for gs_apply_ctf; in != out. */
+int gs_fourier_shift(const gs_config* cfg, const float* in, const float* t, int B, float* out, const gs_fft* fft,
+                     void* ws, size_t ws_bytes, gs_stream_t stream);
+
+/* gs_split_gaussians: SplitGaussian of Algorithm 1 for every Gaussian (the optional
+ * densification that doubles N): out[2N * 11] holds, at rows g and N + g, the children of
+ * Gaussian g, placed at mu +- alpha s_max v along its major axis (v the column of R(q) of the
+ * largest softplus scale s_max, the lower index on ties), each with amplitude A / 2 and the
+ * major scale s_max sqrt(1 - alpha^2); the other scales and the rotation are kept.  The pair
+ * keeps the parent's mass, mean and covariance.  Raw parameters (softplus inverted in FP64).
+ * 0 <= alpha < 1; out != theta. */
+int gs_split_gaussians(const float* theta, int N, float alpha, float* out, gs_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

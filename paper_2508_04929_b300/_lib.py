@@ -82,6 +82,8 @@ _SIGS = {
     "gs_mlp_forward": [_P, _I, _I, _I, _P, _P, _I, _P, _P, _P],
     "gs_mlp_backward": [_P, _I, _I, _I, _P, _P, _I, _P, _P, _P, _P, _P],
     "gs_mse": [_P, _P, _P, _I, _I, _F, _P, _P, _P],
+    "gs_fourier_shift": [_CFG, _P, _P, _I, _P, ctypes.POINTER(GsFFT), _P, _S, _P],
+    "gs_split_gaussians": [_P, _I, _F, _P, _P],
     "gs_voxel_workspace_size": [_I, ctypes.POINTER(_S)],
     "gs_voxelize": [_P, _I, _I, _F, _F, _P, _P, _S, _P],
     "gs_fsc_create": [_I, ctypes.POINTER(GsFSC)],
@@ -317,3 +319,18 @@ def gs_fsc_workspace_size(f: GsFSC) -> int:
 def gs_fsc(f: GsFSC, vol1, vol2, out, ws, stream=None) -> None:
     _check("gs_fsc", lib.gs_fsc(ctypes.byref(f), _ptr(vol1), _ptr(vol2), _ptr(out), _ptr(ws),
                                 ws.numel() * ws.element_size(), _stream(stream)))
+
+
+# ---------------------------------------------------------------------------------------
+# Algorithm 1: FourierShift and SplitGaussian
+# ---------------------------------------------------------------------------------------
+def gs_fourier_shift(cfg, inp, t, out, fft, ws, stream=None) -> None:
+    B = inp.shape[0]
+    _check("gs_fourier_shift", lib.gs_fourier_shift(ctypes.byref(cfg), _ptr(inp), _ptr(t), B, _ptr(out),
+                                                    ctypes.byref(fft), _ptr(ws), ws.numel() * ws.element_size(),
+                                                    _stream(stream)))
+
+
+def gs_split_gaussians(theta, out, alpha=0.5, stream=None) -> None:
+    _check("gs_split_gaussians", lib.gs_split_gaussians(_ptr(theta), theta.shape[0], float(alpha), _ptr(out),
+                                                        _stream(stream)))

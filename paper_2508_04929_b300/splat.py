@@ -86,6 +86,11 @@ class Splatter:
         L.gs_apply_ctf(self.cfg, inp, ctf, out, self.fft, self.ws)
         return out
 
+    def fourier_shift(self, inp, t, out):
+        """out = inp moved by t[B, 2] (model units), FourierShift of Algorithm 1."""
+        L.gs_fourier_shift(self.cfg, inp, t, out, self.fft, self.ws)
+        return out
+
     def loss_grad(self, X, Y):
         L.gs_loss(self.cfg, X, Y, self.loss, self.dX)
         return self.loss[: self.B], self.dX
