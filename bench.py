@@ -64,6 +64,9 @@ def parse():
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--mixed", type=int, default=1, help="also time the mixed-size batch (1/0)")
     p.add_argument("--cpu-sample", type=int, default=0, help="images in the CPU sample (0 = one per core, max 16)")
+    p.add_argument("--dp", action="store_true",
+                   help="time a data-parallel training step (all-reduce of dL/dTheta before Adam) instead of "
+                        "independent replicas")
     return p.parse_args()
 
 
@@ -362,11 +365,16 @@ def main():
     # --- batched, fused form: the whole step as one CUDA graph (autotuned launch shape) ---
     from paper_2508_04929_b300.batched import GraphStep, Problem
     prob = Problem(D=args.D, theta=t.clone(), W=W.clone(), ctf=C.clone(), Y=Y, tile=tile, chunk=chunk)
-    gs = GraphStep([prob], adam=True)
+    gs = GraphStep([prob], adam=not args.dp)
     sp = prob.sp
     stream = torch.cuda.current_stream()
+    step = gs.replay
+    if args.dp:  # replicated Theta, one all-reduce of dL/dTheta per step, replicated Adam
+        from paper_2508_04929_b300 import distributed as DPm
+        dps = DPm.DataParallelStep(prob.theta, *DPm.graph_step_parts(gs))
+        step = dps
     for _ in range(max(args.warmup, 3)):
-        gs.replay()
+        step()
     torch.cuda.synchronize()
     st = gs.check()
     # algorithmic work: Gaussian-pixel evaluations inside the support boxes of this batch
@@ -382,7 +390,7 @@ def main():
     with ClockSampler(local) as clk:
         e0.record(stream)
         for _ in range(args.steps):
-            gs.replay()
+            step()
         e1.record(stream)
         torch.cuda.synchronize()
         ms_total = e0.elapsed_time(e1)
@@ -480,7 +488,8 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(workload(args), tile=tile, chunk=chunk, parallelism="replicas" if world > 1 else "single"),
+            "config": dict(workload(args), tile=tile, chunk=chunk,
+                           parallelism=("dp" if args.dp else "replicas") if world > 1 else ("dp1" if args.dp else "single")),
             "plain_form": {"value": plain, "unit": UNIT, "form": "one particle per launch sequence, Adam per image"},
             "speedup_vs_plain": (value / world / plain) if plain else None,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
