@@ -40,6 +40,7 @@ import torch
 
 from . import _lib as L
 from . import synth
+from . import volume
 from .splat import Splatter
 
 DIN, HIDDEN, DOUT = 32, 128, 10
@@ -125,6 +126,19 @@ class PointMLP:
         net.params.copy_(torch.from_numpy(np.asarray(st["params"], dtype=np.float32)))
         return net
 
+    @classmethod
+    def load(cls, path, device="cuda"):
+        with np.load(path) as f:
+            return cls.from_state({"dims": f["dims"], "params": f["params"]}, device)
+
+
+def load_pretrained(device="cuda"):
+    """The network trained by ``python -m paper_2508_04929_b300.warmstart --molecules 2000``
+    (D = 128, N 5k-50k, 39M labelled seeds), shipped with the package."""
+    import os
+    return PointMLP.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "pointmlp_d128.npz"),
+                         device)
+
 
 # --------------------------------------------------------------------------------- data
 @dataclass
@@ -201,7 +215,7 @@ def eval_schedule(steps, every=25, fine_until=100, fine_every=5):
 
 
 def fit(sp: Splatter, theta0, mol: Molecule, steps, lr=1e-3, eval_every=0, eval_idx=None, train_idx=None,
-        seed=0, eval_at=None):
+        seed=0, eval_at=None, snapshot_at=(), snapshots=None):
     """The plain method: Adam (one learning rate for all parameters, Sec. 4.1) on the
     summed squared error of minibatches of sp.B particles.  Returns (theta, steps, losses)
     with the evaluation loss recorded at the steps ``eval_at`` (or every ``eval_every``
@@ -225,7 +239,10 @@ def fit(sp: Splatter, theta0, mol: Molecule, steps, lr=1e-3, eval_every=0, eval_
     rec_s, rec_l = [], []
     B = sp.B
     pos = 0
+    snap = set(snapshot_at)
     for step in range(steps + 1):
+        if step in snap and snapshots is not None:
+            snapshots[step] = theta.clone()
         if step in eval_at:
             rec_s.append(step)
             rec_l.append(eval_loss(sp, theta, mol, eval_idx))
@@ -392,7 +409,7 @@ def steps_to_target(steps, losses, target):
 
 
 def compare_starts(sp: Splatter, mol: Molecule, net: PointMLP, rng, steps=1500, eval_every=25, lr=3e-3,
-                   n_eval=64, eval_at=None):
+                   n_eval=64, eval_at=None, fsc_at=(), apix=1.5):
     """Fits of one molecule from the random init, from bare seeds and from the learned
     start.  The target is 1.01 x the loss the random-init fit converges to, taken as the
     lowest evaluation loss of its run (the fit of a finite particle set overfits after
@@ -409,10 +426,16 @@ def compare_starts(sp: Splatter, mol: Molecule, net: PointMLP, rng, steps=1500, 
         "seeds": seed_theta(draw_seeds(vol, N, rng)[0], mass),
         "learned": initial_theta(sp, mol, N, rng, net, idx=train_idx),
     }
+    vol_gt = volume.voxelize(mol.theta_gt, sp.D) if fsc_at else None
     for name, th0 in starts.items():
+        snaps = {}
         _, s, l = fit(sp, th0, mol, steps, lr=lr, eval_every=eval_every, eval_idx=eval_idx, train_idx=train_idx,
-                      eval_at=eval_at)
+                      eval_at=eval_at, snapshot_at=fsc_at, snapshots=snaps)
         out[name] = {"steps": s, "loss": l}
+        if fsc_at:
+            # the fitted mixture against the ground truth: FSC 0.5 resolution (Angstrom) per step
+            out[name]["res_fsc05"] = {int(k): volume.resolution(volume.fsc(volume.voxelize(v, sp.D), vol_gt).cpu(),
+                                                                apix, 0.5) for k, v in snaps.items()}
     conv = float(np.min(out["random"]["loss"]))
     target = 1.01 * conv
     for name in starts:
@@ -449,23 +472,33 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--out", default=None, help="write the full result (JSON) here")
     ap.add_argument("--save-net", default=None, help="write the trained network (npz) here")
+    ap.add_argument("--net", default=None,
+                    help="evaluate this trained network (npz; 'pretrained' for the shipped one) instead of building a "
+                         "dataset and training")
+    ap.add_argument("--fsc-at", default="0,25,100,400",
+                    help="steps at which the fits are compared with the ground truth by FSC")
     a = ap.parse_args(argv)
+    fsc_at = tuple(int(x) for x in a.fsc_at.split(",") if x.strip())
     dev = "cuda"
 
     def log(msg):
         print(msg, file=sys.stderr, flush=True)
 
-    data, t_data = _timed(lambda: build_dataset(a.molecules, D=a.D, N_range=(a.n_min, a.n_max), P=a.particles,
-                                                batch=a.batch, fit_steps=a.fit_steps, lr=a.lr, seed=a.seed,
-                                                device=dev, log=log))
-    log(f"dataset: {data.X.shape[0]} seeds from {a.molecules} molecules in {t_data:.1f}s")
-    net = PointMLP(seed=a.seed, device=dev)
-    (curve, val), t_train = _timed(lambda: train(net, data, epochs=a.epochs, lr=2e-3, seed=a.seed, log=log))
-    log(f"trained {a.epochs} epochs in {t_train:.1f}s, validation mse {val:.4f}")
-    if a.save_net:
-        np.savez(a.save_net, dims=np.asarray(net.dims), params=net.state()["params"])
-    samples = data.X.shape[0]
-    del data
+    if a.net:
+        net = load_pretrained(dev) if a.net == "pretrained" else PointMLP.load(a.net, dev)
+        curve, val, t_data, t_train, samples = [], float("nan"), 0.0, 0.0, 0
+    else:
+        data, t_data = _timed(lambda: build_dataset(a.molecules, D=a.D, N_range=(a.n_min, a.n_max), P=a.particles,
+                                                    batch=a.batch, fit_steps=a.fit_steps, lr=a.lr, seed=a.seed,
+                                                    device=dev, log=log))
+        log(f"dataset: {data.X.shape[0]} seeds from {a.molecules} molecules in {t_data:.1f}s")
+        net = PointMLP(seed=a.seed, device=dev)
+        (curve, val), t_train = _timed(lambda: train(net, data, epochs=a.epochs, lr=2e-3, seed=a.seed, log=log))
+        log(f"trained {a.epochs} epochs in {t_train:.1f}s, validation mse {val:.4f}")
+        if a.save_net:
+            np.savez(a.save_net, dims=np.asarray(net.dims), params=net.state()["params"])
+        samples = data.X.shape[0]
+        del data
 
     rng = np.random.default_rng([a.seed, 7919])
     Ns = np.exp(rng.uniform(math.log(a.n_min), math.log(a.n_max), a.eval_molecules)).astype(int)
@@ -475,17 +508,19 @@ def main(argv=None):
     for i, N in enumerate(Ns):
         mrng = np.random.default_rng([a.seed, 104729, i])
         mol = simulate(sp, int(N), a.particles, mrng, device=dev, seed=10 ** 6 + i)
-        res = compare_starts(sp, mol, net, mrng, steps=a.eval_steps, lr=a.lr, eval_at=sched)
+        res = compare_starts(sp, mol, net, mrng, steps=a.eval_steps, lr=a.lr, eval_at=sched, fsc_at=fsc_at)
         tr = torch.arange(0, a.particles - 64, device=dev)
         _, t_warm = _timed(lambda: initial_theta(sp, mol, int(N), mrng, net, idx=tr))
         _, t_steps = _timed(lambda: fit(sp, random_theta(int(N), mrng, dev), mol, 100, lr=a.lr, train_idx=tr))
         row = {"N": int(N), "target": res["target"], "warm_start_ms": 1e3 * t_warm, "adam_step_ms": 10.0 * t_steps}
         for k in ("random", "seeds", "learned"):
             row[k] = {"steps_to_target": res[k]["steps_to_target"], "loss0": res[k]["loss"][0],
-                      "best": float(np.min(res[k]["loss"])), "steps": res[k]["steps"], "loss": res[k]["loss"]}
+                      "best": float(np.min(res[k]["loss"])), "steps": res[k]["steps"], "loss": res[k]["loss"],
+                      "res_fsc05": res[k].get("res_fsc05", {})}
         rows.append(row)
         log(f"molecule N={N}: steps to target random {row['random']['steps_to_target']} seeds "
-            f"{row['seeds']['steps_to_target']} learned {row['learned']['steps_to_target']}")
+            f"{row['seeds']['steps_to_target']} learned {row['learned']['steps_to_target']}; FSC-0.5 resolution (A) "
+            f"by step: " + "; ".join(f"{k} {row[k]['res_fsc05']}" for k in ("random", "seeds", "learned")))
     sp.close()
 
     def agg(k):
@@ -493,12 +528,16 @@ def main(argv=None):
         ok = [x for x in v if x is not None]
         return {"median": float(np.median(ok)) if ok else None, "reached": len(ok), "of": len(v)}
 
+    training = ({"network": a.net} if a.net else
+                {"molecules": a.molecules, "fit_steps": a.fit_steps, "training_seeds": int(samples),
+                 "dataset_s": round(t_data, 1), "train_s": round(t_train, 1), "val_mse": val})
     summary = {
-        "experiment": "learned warm start", "D": a.D, "molecules": a.molecules, "N_range": [a.n_min, a.n_max],
-        "particles": a.particles, "fit_steps": a.fit_steps, "lr": a.lr, "training_seeds": int(samples),
-        "dataset_s": round(t_data, 1), "train_s": round(t_train, 1), "val_mse": val,
+        "experiment": "learned warm start", "D": a.D, "N_range": [a.n_min, a.n_max], "particles": a.particles,
+        "lr": a.lr, "eval_molecules": a.eval_molecules, **training,
         "steps_to_target": {k: agg(k) for k in ("random", "seeds", "learned")},
         "learned_best_below_random_best": sum(r["learned"]["best"] < r["random"]["best"] for r in rows),
+        "fsc05_resolution_median_A": {k: {st: float(np.median([r[k]["res_fsc05"][st] for r in rows]))
+                                          for st in fsc_at} for k in ("random", "seeds", "learned")},
         "warm_start_ms_median": float(np.median([r["warm_start_ms"] for r in rows])),
         "adam_step_ms_median": float(np.median([r["adam_step_ms"] for r in rows])),
     }
