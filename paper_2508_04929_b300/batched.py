@@ -163,3 +163,40 @@ class GraphStep:
         for p in self.problems:
             if p.sp is not None:
                 p.sp.close()
+
+
+class HostFeeder:
+    """Double-buffered feeding of one problem of a GraphStep from pinned host memory: the
+    next step's (W, ctf, Y) are copied host -> device on a side stream while the current step
+    runs, and ``load()`` moves them into the graph's static buffers (a device-to-device copy on
+    the current stream) just before the replay."""
+
+    def __init__(self, gs: GraphStep, i=0):
+        p = gs.problems[i]
+        self.gs, self.i = gs, i
+        self.copy_stream = torch.cuda.Stream(device=p.theta.device)
+        self.bufs = [tuple(torch.empty_like(x) for x in (p.W, p.ctf, p.Y)) for _ in range(2)]
+        self.ready = [torch.cuda.Event() for _ in range(2)]
+        self.free = [torch.cuda.Event() for _ in range(2)]
+        self.filled = 0
+        self.used = 0
+
+    def prefetch(self, W, ctf, Y):
+        """Start copying one step's pinned host inputs (W[B, 9], ctf[B, 5], Y[B, D, D])."""
+        j = self.filled % 2
+        self.copy_stream.wait_event(self.free[j])  # its previous contents have been loaded
+        with torch.cuda.stream(self.copy_stream):
+            for dst, src in zip(self.bufs[j], (W, ctf, Y)):
+                dst.copy_(src, non_blocking=True)
+        self.ready[j].record(self.copy_stream)
+        self.filled += 1
+
+    def load(self):
+        """Make the oldest prefetched inputs the problem's current inputs (stream-ordered)."""
+        j = self.used % 2
+        cur = torch.cuda.current_stream()
+        cur.wait_event(self.ready[j])
+        W, ctf, Y = self.bufs[j]
+        self.gs.load(self.i, W=W, ctf=ctf, Y=Y)
+        self.free[j].record(cur)
+        self.used += 1
