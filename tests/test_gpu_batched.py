@@ -133,3 +133,28 @@ def test_overflow_is_detected_and_rerecorded():
     le, ge = _eager(48, host)
     assert np.allclose(gs.problems[0].sp.loss[:4].cpu().numpy(), le, rtol=1e-6)
     gs.close()
+
+
+def test_autotuner_candidates_and_choice():
+    """The tuner times tile 8 once (its kernels take no chunk depth), every admissible
+    (16 or 32, chunk) pair otherwise, returns the fastest, and a GraphStep built with
+    tile = chunk = 0 takes that choice and reproduces the images of another launch shape."""
+    from paper_2508_04929_b300.autotune import tune
+    p, host = _problem(60, 48, 600, 3)
+    out = tune(48, 600, 3, p.theta, p.W, p.ctf, p.Y, tiles=(8, 16, 32), chunks=(64, 128))
+    shapes = [(r["tile"], r["chunk"]) for r in out["table"]]
+    assert shapes == [(8, 64), (16, 64), (16, 128), (32, 64), (32, 128)]
+    assert all(r["ms"] > 0 for r in out["table"])
+    best = min(out["table"], key=lambda r: r["ms"])
+    assert (out["tile"], out["chunk"]) == (best["tile"], best["chunk"])
+    q, _ = _problem(60, 48, 600, 3, tile=0, chunk=0)
+    gs = GraphStep([q], adam=False, autotune_chunks=(64, 128))
+    assert (q.tile, q.chunk) in shapes
+    gs.replay()
+    torch.cuda.synchronize()
+    Q_tuned = q.sp.Q[:3].clone()
+    ref = Splatter(48, 600, 3, tile=32 if q.tile != 32 else 8, chunk=64)
+    ref.forward(p.theta, p.W, p.ctf, grow=True)
+    torch.cuda.synchronize()
+    assert torch.equal(Q_tuned, ref.Q[:3])  # the support rule does not depend on the tile
+    ref.close()
