@@ -378,7 +378,7 @@ def main():
     torch.cuda.synchronize()
     st = gs.check()
     # algorithmic work: Gaussian-pixel evaluations inside the support boxes of this batch
-    box = sp.proj.view(torch.int16).view(args.B, args.N, 16)[:, :, 12:16].to(torch.int64)
+    box = sp.proj[: args.B * args.N * 32].view(torch.int16).view(args.B, args.N, 16)[:, :, 12:16].to(torch.int64)
     area = ((box[..., 1] - box[..., 0] + 1).clamp(min=0) * (box[..., 3] - box[..., 2] + 1).clamp(min=0))
     e_alg = int(area.sum())
     n_pairs = int(sp.n_pairs.item()) & 0xFFFFFFFF

@@ -94,6 +94,14 @@ typedef struct gs_fft {
 /* Number of tiles per image, ceil(D / tile)^2, into *n.  GS_EINVAL on a bad config. */
 int gs_tiles_per_image(const gs_config* cfg, int* n);
 
+/* Bytes of the projection buffer that gs_project fills for B particles and N Gaussians:
+ * the B*N records (gs_record, particle-major), then, at byte offset 32*B*N, the B*N
+ * support boxes again as int32 pairs {x0 | x1 << 16, y0 | y1 << 16} (8 bytes each,
+ * particle-major, the same values as the records' boxes).  The binning calls read the
+ * boxes from that plane, a quarter of the bytes of the records.  GS_EINVAL if B or N is
+ * negative. */
+int gs_proj_size(int B, int N, size_t* bytes);
+
 /* Workspace bytes for batches of up to B particles and N Gaussians with the given cuFFT
  * work area (gs_fft.work_bytes, 0 if gs_apply_ctf is not used).  The workspace holds the
  * status word, the activated Gaussians, the binning histograms, the per-(particle,
@@ -120,8 +128,9 @@ int gs_clear_status(void* ws, gs_stream_t stream);
 
 /* BuildGaussians + ViewingTransform + Projection (Algorithm 2; Sec. 3.3.1-3.3.3, Eqs. 5, 6,
  * 8; App. A.2 Eqs. 12-13).
- * theta[N*11] raw parameters, W[B*9] poses -> proj[B*N] records (gs_record, particle-major:
- * proj[b*N + g]).  Also fills the activated-Gaussian table in `ws` used by gs_render_bwd.
+ * theta[N*11] raw parameters, W[B*9] poses -> proj: the B*N records (gs_record,
+ * particle-major: proj[b*N + g]) followed by the box plane (gs_proj_size(B, N) bytes in
+ * all).  Also fills the activated-Gaussian table in `ws` used by gs_render_bwd.
  * The support box is computed in FP32 in this order, every operation correctly rounded:
  *   s = fp32(softplus(s_raw) in FP64);  n = sqrt(((qw*qw + qx*qx) + qy*qy) + qz*qz);
  *   (w,x,y,z) = q / n;  R from (w,x,y,z) with the pairwise products formed first,
@@ -146,7 +155,8 @@ int gs_project(const gs_config* cfg, const float* theta, int N, const float* W, 
  * (T = gs_tiles_per_image); *n_pairs (device uint32) the number of instances needed.
  * If that exceeds pair_capacity the extra instances are dropped, the ranges are clipped
  * to pair_capacity and GS_STATUS_OVERFLOW is set.  Requires ceil(D/tile) <= 64 and
- * N * T < 2^32 (GS_EINVAL otherwise). */
+ * N * T < 2^32 (GS_EINVAL otherwise).  proj is gs_project's whole output for the same B
+ * and N: the supports are read from its box plane. */
 int gs_bin_sort(const gs_config* cfg, const gs_record* proj, int B, int N, void* ws,
                 size_t ws_bytes, uint32_t* pair_gauss, size_t pair_capacity,
                 uint32_t* tile_ranges, uint32_t* n_pairs, gs_stream_t stream);
@@ -229,7 +239,8 @@ int gs_step_counted(float* theta, const float* dtheta, float* m, float* v, int n
  * before capturing any stream.  All calls on a device share the array and leave their
  * contents in it (the call clears what must start at zero); calls whose GPU work
  * overlaps -- on different streams without ordering -- race on the array.  Overflow of
- * pair_capacity is visible as *n_pairs > pair_capacity (the status word is internal). */
+ * pair_capacity is visible as *n_pairs > pair_capacity (the status word is internal).
+ * proj is gs_project's whole output for the same B and N, box plane included. */
 int gs_bin_sort_noalloc(const gs_config* cfg, const gs_record* proj, int B, int N,
                         uint32_t* pair_gauss, size_t pair_capacity, uint32_t* tile_ranges,
                         uint32_t* n_pairs, gs_stream_t stream, size_t* scratch_needed);

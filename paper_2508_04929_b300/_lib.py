@@ -57,6 +57,7 @@ _S = ctypes.c_size_t
 _CFG = ctypes.POINTER(GsConfig)
 _SIGS = {
     "gs_tiles_per_image": [_CFG, ctypes.POINTER(_I)],
+    "gs_proj_size": [_I, _I, ctypes.POINTER(_S)],
     "gs_workspace_size": [_CFG, _I, _I, _S, ctypes.POINTER(_S)],
     "gs_fft_create": [_I, _I, ctypes.POINTER(GsFFT)],
     "gs_fft_destroy": [ctypes.POINTER(GsFFT)],
@@ -123,6 +124,19 @@ def gs_tiles_per_image(cfg: GsConfig) -> int:
     return n.value
 
 
+def gs_proj_size(B: int, N: int) -> int:
+    """Bytes of gs_project's output buffer: B*N records, then the B*N-box plane."""
+    n = _S()
+    _check("gs_proj_size", lib.gs_proj_size(B, N, ctypes.byref(n)))
+    return n.value
+
+
+def _check_proj(name, proj, B, N):
+    if proj is not None and B > 0 and N > 0 and proj.numel() * proj.element_size() < gs_proj_size(B, N):
+        raise ValueError(f"{name}: proj holds {proj.numel() * proj.element_size()} bytes, "
+                         f"gs_proj_size({B}, {N}) = {gs_proj_size(B, N)}")
+
+
 def gs_workspace_size(cfg: GsConfig, B: int, N: int, fft_work_bytes: int = 0) -> int:
     n = _S()
     _check("gs_workspace_size", lib.gs_workspace_size(ctypes.byref(cfg), B, N, fft_work_bytes, ctypes.byref(n)))
@@ -151,11 +165,13 @@ def gs_clear_status(ws, stream=None) -> None:
 
 def gs_project(cfg, theta, W, proj, ws, stream=None) -> None:
     N, B = theta.shape[0], W.shape[0]
+    _check_proj("gs_project", proj, B, N)
     _check("gs_project", lib.gs_project(ctypes.byref(cfg), _ptr(theta), N, _ptr(W), B, _ptr(proj), _ptr(ws),
                                         ws.numel() * ws.element_size(), _stream(stream)))
 
 
 def gs_bin_sort(cfg, proj, B, N, ws, pair_gauss, tile_ranges, n_pairs, stream=None) -> None:
+    _check_proj("gs_bin_sort", proj, B, N)
     cap = 0 if pair_gauss is None else pair_gauss.numel()
     _check("gs_bin_sort", lib.gs_bin_sort(ctypes.byref(cfg), _ptr(proj), B, N, _ptr(ws),
                                           ws.numel() * ws.element_size(), _ptr(pair_gauss), cap,

@@ -44,6 +44,12 @@ int gs_tiles_per_image(const gs_config* cfg, int* n) {
   return GS_OK;
 }
 
+int gs_proj_size(int B, int N, size_t* bytes) {
+  if (B < 0 || N < 0 || !bytes) return GS_EINVAL;
+  *bytes = (sizeof(gs_record) + sizeof(int2)) * (size_t)B * (size_t)N;
+  return GS_OK;
+}
+
 int gs_workspace_size(const gs_config* cfg, int B, int N, size_t fft_work_bytes, size_t* bytes) {
   if (!cfg_ok(cfg) || !bytes || !sizes_ok(cfg, B, N)) return GS_EINVAL;
   *bytes = ws_layout(*cfg, B, N, fft_work_bytes).total;

@@ -89,7 +89,8 @@ __global__ void k_activate(const float* __restrict__ theta, int N, float* __rest
 constexpr int kProjParticles = 4;  // particles per thread: one load of the Gaussian's row serves them all
 
 __global__ void k_project(const float* __restrict__ gauss, int N, const float* __restrict__ Wall, int B, int D,
-                          float inv_h, float kcut, gs_record* __restrict__ proj, int* __restrict__ status) {
+                          float inv_h, float kcut, gs_record* __restrict__ proj, int2* __restrict__ boxes,
+                          int* __restrict__ status) {
   const int b0 = blockIdx.y * kProjParticles;
   __shared__ float Wsh[kProjParticles * 9];
   if (threadIdx.x < kProjParticles * 9 && b0 + (int)threadIdx.x / 9 < B)
@@ -173,6 +174,9 @@ __global__ void k_project(const float* __restrict__ gauss, int N, const float* _
     const float4* srcp = reinterpret_cast<const float4*>(&r);
     dst[0] = srcp[0];
     dst[1] = srcp[1];
+    // the box again in the plane after the records, for the binning passes
+    boxes[(size_t)b * N + g] = make_int2((int)(((unsigned)(uint16_t)r.x0) | ((unsigned)(uint16_t)r.x1 << 16)),
+                                         (int)(((unsigned)(uint16_t)r.y0) | ((unsigned)(uint16_t)r.y1 << 16)));
   }
   if (any_bad) atomicOr(status, GS_STATUS_NONFINITE);
 }
@@ -189,7 +193,8 @@ cudaError_t launch_project(const gs_config& cfg, const float* gauss, int N, cons
                            gs_record* proj, int* status, cudaStream_t s) {
   if (N <= 0 || B <= 0) return cudaSuccess;
   dim3 grid((N + 255) / 256, (B + kProjParticles - 1) / kProjParticles);
-  k_project<<<grid, 256, 0, s>>>(gauss, N, W, B, cfg.D, inv_pixel(cfg), cfg.cutoff_sigma, proj, status);
+  int2* boxes = reinterpret_cast<int2*>(proj + (size_t)B * N);  // box plane after the B * N records
+  k_project<<<grid, 256, 0, s>>>(gauss, N, W, B, cfg.D, inv_pixel(cfg), cfg.cutoff_sigma, proj, boxes, status);
   return cudaGetLastError();
 }
 

@@ -344,6 +344,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, kFwd8MinBlocks) k_render_fwd8
   const size_t rr = ((size_t)b * ntx * ntx + tile) * 2;
   const uint32_t start = ranges[rr], end = ranges[rr + 1];
   const float4* pr = reinterpret_cast<const float4*>(proj + (size_t)b * N);
+  const uint32_t gmax = (uint32_t)N - 1u;  // pair entries are clamped: a bad list cannot leave proj
   u64 acc[kB][4];
 #pragma unroll
   for (int u = 0; u < kB; ++u)
@@ -354,18 +355,18 @@ __global__ void __launch_bounds__(kTileWarps * 32, kFwd8MinBlocks) k_render_fwd8
   float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na;
   uint32_t g1 = 0;
   if (i < end) {
-    const uint32_t g0 = pair_gauss[i];
+    const uint32_t g0 = min(pair_gauss[i], gmax);
     na = __ldg(pr + 2 * (size_t)g0);
     nb = __ldg(pr + 2 * (size_t)g0 + 1);
   }
-  if (i + 32 < end) g1 = pair_gauss[i + 32];
+  if (i + 32 < end) g1 = min(pair_gauss[i + 32], gmax);
   while (i < end) {
     const Rec r = rec_from(na, nb);
     i += 32;
     if (i < end) {
       na = __ldg(pr + 2 * (size_t)g1);
       nb = __ldg(pr + 2 * (size_t)g1 + 1);
-      if (i + 32 < end) g1 = pair_gauss[i + 32];
+      if (i + 32 < end) g1 = min(pair_gauss[i + 32], gmax);
     }
     Item it = make_item(r, X, Y);
     fwd_item(it, acc);
@@ -398,16 +399,17 @@ __global__ void __launch_bounds__(kTileWarps * 32) k_render_bwd8(const gs_record
   const float kap = -2.f / (kLog2e * h * h);  // P = kap * [[ca, -cb/2], [-cb/2, cc]]
   __syncwarp();
   const float4* pr = reinterpret_cast<const float4*>(proj + (size_t)b * N);
+  const uint32_t gmax = (uint32_t)N - 1u;  // pair entries are clamped: a bad list cannot leave proj / wacc
   float pacc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   uint32_t i = start + lane;
   float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na;
   uint32_t g0 = 0, g1 = 0;
   if (i < end) {
-    g0 = pair_gauss[i];
+    g0 = min(pair_gauss[i], gmax);
     na = __ldg(pr + 2 * (size_t)g0);
     nb = __ldg(pr + 2 * (size_t)g0 + 1);
   }
-  if (i + 32 < end) g1 = pair_gauss[i + 32];
+  if (i + 32 < end) g1 = min(pair_gauss[i + 32], gmax);
   while (i < end) {
     const Rec r = rec_from(na, nb);
     const uint32_t g = g0;
@@ -416,7 +418,7 @@ __global__ void __launch_bounds__(kTileWarps * 32) k_render_bwd8(const gs_record
       g0 = g1;
       na = __ldg(pr + 2 * (size_t)g0);
       nb = __ldg(pr + 2 * (size_t)g0 + 1);
-      if (i + 32 < end) g1 = pair_gauss[i + 32];
+      if (i + 32 < end) g1 = min(pair_gauss[i + 32], gmax);
     }
     Item it = make_item(r, X, Y);
     float S[6];
@@ -457,9 +459,9 @@ __device__ __forceinline__ unsigned block_mask(int x0, int x1, int y0, int y1, c
 __device__ __forceinline__ void stage_chunk(gs_record* rec, uint32_t* gid, uint8_t* msk,
                                             const gs_record* __restrict__ proj, size_t pbase,
                                             const uint32_t* __restrict__ pair_gauss, uint32_t start, int n,
-                                            const Region& reg) {
+                                            const Region& reg, uint32_t gmax) {
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    const uint32_t g = pair_gauss[start + k];
+    const uint32_t g = min(pair_gauss[start + k], gmax);  // a bad list cannot leave proj
     const float4* src = reinterpret_cast<const float4*>(proj + pbase + g);
     float4* dst = reinterpret_cast<float4*>(rec + k);
     const float4 a = __ldg(src), b = __ldg(src + 1);
@@ -513,7 +515,7 @@ __global__ void __launch_bounds__(kRegionWarps * 32) k_render_fwd16(const gs_rec
   for (uint32_t base = start; base < end; base += chunk) {
     const int n = (int)min((uint32_t)chunk, end - base);
     __syncthreads();
-    stage_chunk(rec, nullptr, msk, proj, pbase, pair_gauss, base, n, reg);
+    stage_chunk(rec, nullptr, msk, proj, pbase, pair_gauss, base, n, reg, (uint32_t)N - 1u);
     __syncthreads();
     const int cnt = compact_mask(msk, n, warp, list);
     for (int j = (lane - running) & 31; j < cnt; j += 32) {
@@ -560,7 +562,7 @@ __global__ void __launch_bounds__(kRegionWarps * 32) k_render_bwd16(const gs_rec
   for (uint32_t base = start; base < end; base += chunk) {
     const int n = (int)min((uint32_t)chunk, end - base);
     __syncthreads();
-    stage_chunk(rec, gid, msk, proj, pbase, pair_gauss, base, n, reg);
+    stage_chunk(rec, gid, msk, proj, pbase, pair_gauss, base, n, reg, (uint32_t)N - 1u);
     __syncthreads();
     const int cnt = compact_mask(msk, n, warp, list);
     for (int j = lane; j < cnt; j += 32) {

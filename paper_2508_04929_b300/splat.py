@@ -32,7 +32,7 @@ class Splatter:
         ws_bytes = L.gs_workspace_size(self.cfg, self.B, self.N, fw)
         dev = self.device
         self.ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
-        self.proj = torch.empty(max(self.B * self.N, 1) * L.RECORD_BYTES, dtype=torch.uint8, device=dev)
+        self.proj = torch.empty(max(L.gs_proj_size(self.B, self.N), 1), dtype=torch.uint8, device=dev)
         self.ranges = torch.empty(max(self.B * self.Tn * 2, 2), dtype=torch.int32, device=dev)
         self.n_pairs = torch.zeros(1, dtype=torch.int32, device=dev)
         cap = default_pair_capacity(self.B, self.N, tile) if pair_capacity is None else int(pair_capacity)

@@ -248,13 +248,17 @@ def test_invalid_arguments_raise():
     cfg = L.config(64)
     t = torch.zeros(10, 11, device=DEV)
     W = torch.zeros(2, 9, device=DEV)
+    proj = torch.empty(L.gs_proj_size(2, 10), dtype=torch.uint8, device=DEV)
+    assert proj.numel() == 2 * 10 * (32 + 8)  # records, then the box plane
     with pytest.raises(L.GsError):
-        L.gs_project(L.config(64, tile=12), t, W, torch.empty(640, dtype=torch.uint8, device=DEV),
-                     torch.empty(1 << 20, dtype=torch.uint8, device=DEV))
+        L.gs_project(L.config(64, tile=12), t, W, proj, torch.empty(1 << 20, dtype=torch.uint8, device=DEV))
     small_ws = torch.empty(256, dtype=torch.uint8, device=DEV)
     with pytest.raises(L.GsError) as e:
-        L.gs_project(cfg, t, W, torch.empty(640, dtype=torch.uint8, device=DEV), small_ws)
+        L.gs_project(cfg, t, W, proj, small_ws)
     assert e.value.rc == L.GS_ENOSPC
+    with pytest.raises(ValueError):  # records only, without room for the box plane
+        L.gs_project(cfg, t, W, torch.empty(2 * 10 * 32, dtype=torch.uint8, device=DEV),
+                     torch.empty(1 << 20, dtype=torch.uint8, device=DEV))
 
 
 # ---------------------------------------------------------------------------------------
