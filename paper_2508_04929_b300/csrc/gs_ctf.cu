@@ -94,38 +94,60 @@ __global__ void __cluster_dims__(kLossCtas, 1, 1) k_loss(const float* __restrict
   cluster.sync();  // the other CTAs' shared memory stays alive until it has been read
 }
 
-__global__ void k_adam(float* __restrict__ th, const float* __restrict__ g, float* __restrict__ m,
-                       float* __restrict__ v, int n, float lr, float b1, float b2, float eps, float c1, float c2) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    th[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
-  }
+// One Adam update (Sec. 4.1; bias corrections c1 = 1 / (1 - b1^t), c2 = 1 / (1 - b2^t)).
+__device__ __forceinline__ void adam_one(float& th, float g, float& m, float& v, float lr, float b1, float b2,
+                                         float eps, float c1, float c2) {
+  m = b1 * m + (1.f - b1) * g;
+  v = b2 * v + (1.f - b2) * g * g;
+  th = th - lr * (m * c1) / (sqrtf(v * c2) + eps);
 }
 
-// Adam with the step counter on the device (t_dev = steps already taken), so that a captured
-// graph can be replayed: bias corrections are formed in FP64 once per CTA.
-__global__ void k_adam_counted(float* __restrict__ th, const float* __restrict__ g, float* __restrict__ m,
-                               float* __restrict__ v, int n, const int* __restrict__ t_dev, float lr, float b1,
-                               float b2, float eps) {
-  __shared__ float cc[2];
-  if (threadIdx.x == 0) {
-    const double t = (double)(*t_dev + 1);
-    cc[0] = (float)(1.0 / (1.0 - pow((double)b1, t)));
-    cc[1] = (float)(1.0 / (1.0 - pow((double)b2, t)));
+// Adam over n floats, four per thread and iteration when all buffers are 16-byte aligned
+// (kVec), with a grid of two CTAs per SM.  kCounted: the step counter is on the device
+// (t_dev = steps already taken) so that a captured graph can be replayed; the bias
+// corrections are then formed in FP64 by one thread per CTA.
+template <bool kCounted, bool kVec>
+__global__ void k_adam(float* __restrict__ th, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, int n, const int* __restrict__ t_dev, float lr, float b1, float b2,
+                       float eps, float c1, float c2) {
+  if (kCounted) {
+    __shared__ float cc[2];
+    if (threadIdx.x == 0) {
+      const double t = (double)(*t_dev + 1);
+      cc[0] = (float)(1.0 / (1.0 - pow((double)b1, t)));
+      cc[1] = (float)(1.0 / (1.0 - pow((double)b2, t)));
+    }
+    __syncthreads();
+    c1 = cc[0];
+    c2 = cc[1];
   }
-  __syncthreads();
-  const float c1 = cc[0], c2 = cc[1];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    th[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  int done = 0;
+  if (kVec) {
+    const int n4 = n / 4;
+    float4* th4 = reinterpret_cast<float4*>(th);
+    float4* m4 = reinterpret_cast<float4*>(m);
+    float4* v4 = reinterpret_cast<float4*>(v);
+    const float4* g4 = reinterpret_cast<const float4*>(g);
+    for (int i = tid; i < n4; i += stride) {
+      float4 T = th4[i], M = m4[i], V = v4[i];
+      const float4 G = g4[i];
+      adam_one(T.x, G.x, M.x, V.x, lr, b1, b2, eps, c1, c2);
+      adam_one(T.y, G.y, M.y, V.y, lr, b1, b2, eps, c1, c2);
+      adam_one(T.z, G.z, M.z, V.z, lr, b1, b2, eps, c1, c2);
+      adam_one(T.w, G.w, M.w, V.w, lr, b1, b2, eps, c1, c2);
+      th4[i] = T;
+      m4[i] = M;
+      v4[i] = V;
+    }
+    done = 4 * n4;
+  }
+  for (int i = done + tid; i < n; i += stride) {
+    float T = th[i], M = m[i], V = v[i];
+    adam_one(T, g[i], M, V, lr, b1, b2, eps, c1, c2);
+    th[i] = T;
+    m[i] = M;
+    v[i] = V;
   }
 }
 
@@ -133,12 +155,27 @@ __global__ void k_count_step(int* t_dev) { *t_dev += 1; }
 
 }  // namespace
 
+// Grid for the Adam kernels: two CTAs per SM at most (grid-stride loops).
+static int adam_blocks(int n) {
+  int blocks = (n / 4 + 255) / 256;
+  const int cap = 2 * num_sms();
+  if (blocks > cap) blocks = cap;
+  return blocks < 1 ? 1 : blocks;
+}
+
+static bool all16(const void* a, const void* b, const void* c, const void* d) {
+  return ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(c) |
+           reinterpret_cast<uintptr_t>(d)) & 15) == 0;
+}
+
 cudaError_t launch_adam_counted(float* theta, const float* g, float* m, float* v, int n, int* t_dev, float lr,
                                 float b1, float b2, float eps, cudaStream_t s) {
   if (n > 0) {
-    int blocks = (n + 255) / 256;
-    if (blocks > 148 * 16) blocks = 148 * 16;
-    k_adam_counted<<<blocks, 256, 0, s>>>(theta, g, m, v, n, t_dev, lr, b1, b2, eps);
+    const int blocks = adam_blocks(n);
+    if (all16(theta, g, m, v))
+      k_adam<true, true><<<blocks, 256, 0, s>>>(theta, g, m, v, n, t_dev, lr, b1, b2, eps, 0.f, 0.f);
+    else
+      k_adam<true, false><<<blocks, 256, 0, s>>>(theta, g, m, v, n, t_dev, lr, b1, b2, eps, 0.f, 0.f);
   }
   k_count_step<<<1, 1, 0, s>>>(t_dev);
   return cudaGetLastError();
@@ -166,9 +203,11 @@ cudaError_t launch_loss(const gs_config& cfg, const float* X, const float* Y, in
 cudaError_t launch_adam(float* theta, const float* g, float* m, float* v, int n, float lr, float b1, float b2,
                         float eps, float c1, float c2, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  int blocks = (n + 255) / 256;
-  if (blocks > 148 * 16) blocks = 148 * 16;
-  k_adam<<<blocks, 256, 0, s>>>(theta, g, m, v, n, lr, b1, b2, eps, c1, c2);
+  const int blocks = adam_blocks(n);
+  if (all16(theta, g, m, v))
+    k_adam<false, true><<<blocks, 256, 0, s>>>(theta, g, m, v, n, nullptr, lr, b1, b2, eps, c1, c2);
+  else
+    k_adam<false, false><<<blocks, 256, 0, s>>>(theta, g, m, v, n, nullptr, lr, b1, b2, eps, c1, c2);
   return cudaGetLastError();
 }
 

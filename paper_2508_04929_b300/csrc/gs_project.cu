@@ -10,8 +10,9 @@
 // The support box is an integer decision.  It is computed with explicitly rounded FP32
 // intrinsics (no FMA contraction) in a fixed order, so that any FP32 implementation of the
 // same sequence reproduces it bit for bit (the order is spelled out in include/gs.h).  The
-// four activations are evaluated in FP64 and rounded once, so that they are the correctly
-// rounded FP32 values with overwhelming probability.
+// three scale activations, which the box depends on, are evaluated in FP64 and rounded
+// once, so that they are the correctly rounded FP32 values with overwhelming probability;
+// the amplitude only scales values and is activated in FP32.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -36,7 +37,7 @@ __global__ void k_activate(const float* __restrict__ theta, int N, float* __rest
   float s0 = (float)softplus_d((double)th[3]);
   float s1 = (float)softplus_d((double)th[4]);
   float s2 = (float)softplus_d((double)th[5]);
-  float A = (float)softplus_d((double)th[10]);
+  const float A = fmaxf(th[10], 0.f) + log1pf(expf(-fabsf(th[10])));
 
   float qw = th[6], qx = th[7], qy = th[8], qz = th[9];
   float n2 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(qw, qw), __fmul_rn(qx, qx)), __fmul_rn(qy, qy)),
