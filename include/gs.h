@@ -104,8 +104,8 @@ int gs_proj_size(int B, int N, size_t* bytes);
 
 /* Workspace bytes for batches of up to B particles and N Gaussians with the given cuFFT
  * work area (gs_fft.work_bytes, 0 if gs_apply_ctf is not used).  The workspace holds the
- * status word, the activated Gaussians, the binning histograms, the per-(particle,
- * Gaussian) gradient partials, the half spectra and the cuFFT work area.  It must be
+ * status word, the activated Gaussians, the binning histograms, the per-Gaussian
+ * gradient accumulator, two batches of half spectra and the cuFFT work area.  It must be
  * 256-byte aligned; its contents need no initialization. */
 int gs_workspace_size(const gs_config* cfg, int B, int N, size_t fft_work_bytes, size_t* bytes);
 
@@ -183,6 +183,20 @@ int gs_apply_ctf(const gs_config* cfg, const float* in, const float* ctf, int B,
  * dLdX may be NULL (loss only). */
 int gs_loss(const gs_config* cfg, const float* X, const float* Y, int B, float* loss,
             float* dLdX, gs_stream_t stream);
+
+/* ApplyCTF, Loss and the adjoint ApplyCTF of a training step in one call (App. A.2 Eq. 14;
+ * Sec. 3.3.5), for callers that need loss[b] and dL/dQ but not X.  With the unnormalized
+ * R2C spectra Q_hat, Y_hat and Z = H_hat Q_hat - Y_hat (the spectrum of X - Y, H_hat being
+ * real and even), Parseval's identity gives loss[b] = s * sum over the full spectrum
+ * |Z|^2 / D^2 (s = 1 for reduction 0, 1 / D^2 for reduction 1), and
+ * dLdQ = C2R(2 s H_hat Z) / D^2 is the adjoint CTF of dL/dX = 2 s (X - Y): the values of
+ * gs_apply_ctf + gs_loss + gs_apply_ctf up to FP32 rounding, with three FFTs instead of
+ * four.  Q, Y, dLdQ [B * D * D]; ctf as for gs_apply_ctf; dLdQ may alias Q.  Uses cuFFT
+ * (fft created for this D and B) and two half spectra plus the work area at the tail of
+ * ws (gs_workspace_size includes them). */
+int gs_ctf_loss_grad(const gs_config* cfg, const float* Q, const float* Y, const float* ctf, int B,
+                     float* loss, float* dLdQ, const gs_fft* fft, void* ws, size_t ws_bytes,
+                     gs_stream_t stream);
 
 /* Backward of Rasterize (App. A.2 Eqs. 16-21; grad_mu = W^T [grad_mu_tilde; 0]; the s, q
  * chain through Sigma = (R S)(R S)^T; softplus derivatives).  Accumulates (+=) dL/dtheta

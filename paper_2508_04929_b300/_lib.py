@@ -68,6 +68,7 @@ _SIGS = {
     "gs_render_fwd": [_CFG, _P, _I, _P, _P, _I, _P, _P],
     "gs_apply_ctf": [_CFG, _P, _P, _I, _P, ctypes.POINTER(GsFFT), _P, _S, _P],
     "gs_loss": [_CFG, _P, _P, _I, _P, _P, _P],
+    "gs_ctf_loss_grad": [_CFG, _P, _P, _P, _I, _P, _P, ctypes.POINTER(GsFFT), _P, _S, _P],
     "gs_render_bwd": [_CFG, _P, _I, _P, _I, _P, _P, _P, _P, _P, _P, _S, _P],
     "gs_render_bwd_pose": [_CFG, _P, _I, _P, _I, _P, _P, _P, _P, _P, _P, _P, _S, _P],
     "gs_step": [_P, _P, _P, _P, _I, _I, _F, _F, _F, _F, _P],
@@ -193,6 +194,13 @@ def gs_apply_ctf(cfg, inp, ctf, out, fft, ws, stream=None) -> None:
 def gs_loss(cfg, X, Y, loss, dLdX=None, stream=None) -> None:
     _check("gs_loss", lib.gs_loss(ctypes.byref(cfg), _ptr(X), _ptr(Y), X.shape[0], _ptr(loss), _ptr(dLdX),
                                   _stream(stream)))
+
+
+def gs_ctf_loss_grad(cfg, Q, Y, ctf, loss, dLdQ, fft, ws, stream=None) -> None:
+    """CTF, loss and adjoint CTF of a training step: loss[B] and dLdQ, without X."""
+    _check("gs_ctf_loss_grad", lib.gs_ctf_loss_grad(ctypes.byref(cfg), _ptr(Q), _ptr(Y), _ptr(ctf), Q.shape[0],
+                                                    _ptr(loss), _ptr(dLdQ), ctypes.byref(fft), _ptr(ws),
+                                                    ws.numel() * ws.element_size(), _stream(stream)))
 
 
 def gs_render_bwd(cfg, theta, W, proj, pair_gauss, tile_ranges, dLdQ, dtheta, ws, stream=None) -> None:

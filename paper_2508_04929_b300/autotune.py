@@ -21,13 +21,13 @@ def tune(D, N, B, theta, W, ctf, Y, device="cuda", tiles=(8, 16, 32), chunks=(64
         for chunk in (chunks[:1] if tile == 8 else chunks):
             sp = Splatter(D, N, B, tile=tile, chunk=chunk, device=device)
             dth = torch.zeros_like(theta)
-            sp.forward_backward(theta, W, ctf, Y, dth, grow=True)
+            sp.forward_backward(theta, W, ctf, Y, dth, grow=True, fused=True)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             for _ in range(iters):
                 dth.zero_()
-                sp.forward_backward(theta, W, ctf, Y, dth, grow=False)
+                sp.forward_backward(theta, W, ctf, Y, dth, grow=False, fused=True)
             e1.record()
             torch.cuda.synchronize()
             results.append({"tile": tile, "chunk": chunk, "ms": e0.elapsed_time(e1) / iters})

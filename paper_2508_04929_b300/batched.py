@@ -4,8 +4,8 @@
 a volume (theta, N Gaussians) with its own box size D and a batch of B particles with
 their own poses, CTF parameters and observed images -- into a single CUDA graph:
 
-    per problem: zero grad -> gs_project -> gs_bin_sort -> gs_render_fwd -> gs_apply_ctf
-                 -> gs_loss -> gs_apply_ctf (adjoint) -> gs_render_bwd -> gs_step_counted
+    per problem: zero grad -> gs_project -> gs_bin_sort -> gs_render_fwd -> gs_ctf_loss_grad
+                 (CTF, loss, adjoint CTF) -> gs_render_bwd -> gs_step_counted
 
 Problems of a mixed batch (different D and N) run on their own streams inside the graph,
 so small volumes overlap large ones; one ``replay()`` launches the whole batch.  Inputs
@@ -94,9 +94,7 @@ class GraphStep:
         sp.project(p.theta, p.W)
         sp.bin_sort(grow=False)
         sp.render()
-        sp.apply_ctf(sp.Q, p.ctf, sp.X)
-        sp.loss_grad(sp.X, p.Y)
-        sp.apply_ctf(sp.dX, p.ctf, sp.dQ)
+        sp.ctf_loss_grad(sp.Q, p.ctf, p.Y)
         sp.backward(p.theta, p.W, sp.dQ, p.dtheta)
         if self.adam:
             L.gs_step_counted(p.theta, p.dtheta, p.m, p.v, p.t, lr=p.lr)

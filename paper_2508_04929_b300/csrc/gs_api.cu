@@ -171,6 +171,33 @@ int gs_apply_ctf(const gs_config* cfg, const float* in, const float* ctf, int B,
   return GS_OK;
 }
 
+int gs_ctf_loss_grad(const gs_config* cfg, const float* Q, const float* Y, const float* ctf, int B, float* loss,
+                     float* dLdQ, const gs_fft* fft, void* ws, size_t ws_bytes, gs_stream_t stream) {
+  if (!cfg_ok(cfg) || B < 0 || B > 65535) return GS_EINVAL;
+  if (B == 0) return GS_OK;
+  if (!Q || !Y || !ctf || !loss || !dLdQ || !fft || !ws || !aligned(ws, 256)) return GS_EINVAL;
+  if (fft->D != cfg->D || fft->B != B) return GS_EINVAL;
+  // two half spectra and the cuFFT work area at the tail of the workspace
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t spec_bytes = align256(2 * sizeof(float) * (size_t)B * cfg->D * (cfg->D / 2 + 1));
+  const size_t need = 2 * spec_bytes + align256(fft->work_bytes);
+  if (ws_bytes < need) return GS_ENOSPC;
+  const size_t off = (ws_bytes - need) & ~size_t(255);
+  float2* specY = ws_ptr<float2>(ws, off);
+  float2* specQ = ws_ptr<float2>(ws, off + spec_bytes);
+  void* work = ws_ptr<void>(ws, off + 2 * spec_bytes);
+  cufftHandle a = (cufftHandle)fft->r2c, c = (cufftHandle)fft->c2r;
+  if (cufftSetStream(a, s) != CUFFT_SUCCESS || cufftSetStream(c, s) != CUFFT_SUCCESS) return GS_ECUDA;
+  if (cufftSetWorkArea(a, work) != CUFFT_SUCCESS || cufftSetWorkArea(c, work) != CUFFT_SUCCESS) return GS_ECUDA;
+  if (cufftExecR2C(a, const_cast<float*>(Q), reinterpret_cast<cufftComplex*>(specQ)) != CUFFT_SUCCESS)
+    return GS_ECUDA;
+  if (cufftExecR2C(a, const_cast<float*>(Y), reinterpret_cast<cufftComplex*>(specY)) != CUFFT_SUCCESS)
+    return GS_ECUDA;
+  if (launch_ctf_loss(*cfg, specQ, specY, ctf, B, loss, s) != cudaSuccess) return GS_ECUDA;
+  if (cufftExecC2R(c, reinterpret_cast<cufftComplex*>(specQ), dLdQ) != CUFFT_SUCCESS) return GS_ECUDA;
+  return GS_OK;
+}
+
 int gs_loss(const gs_config* cfg, const float* X, const float* Y, int B, float* loss, float* dLdX,
             gs_stream_t stream) {
   if (!cfg_ok(cfg) || B < 0) return GS_EINVAL;

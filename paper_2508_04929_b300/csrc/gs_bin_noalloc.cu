@@ -73,7 +73,7 @@ extern "C" int gs_bin_sort_noalloc(const gs_config* cfg, const gs_record* proj, 
   L.ttotal = o; o = align256(o + sizeof(uint32_t) * (size_t)B * full.Tn);
   L.itotal = o; o = align256(o + sizeof(uint32_t) * ((size_t)B + 1));
   L.ibase = o; o = align256(o + sizeof(unsigned long long) * ((size_t)B + 1));
-  L.gauss = L.gacc = L.spec = L.fftwork = L.total = o;
+  L.gauss = L.gacc = L.spec = L.spec2 = L.fftwork = L.total = o;
   if (scratch_needed) *scratch_needed = o;
   if (o > kGsNoallocScratchBytes) return GS_ENOSPC;
 

@@ -15,42 +15,54 @@ namespace cg = cooperative_groups;
 namespace gs {
 namespace {
 
+// Per-image CTF constants, formed in FP64 by one thread: alpha split into hi + lo, beta,
+// sqrt(1 - w^2), w.
+__device__ __forceinline__ void ctf_constants(const float* __restrict__ ctf, int b, int D, float cst[5]) {
+  const double df = ctf[b * 5 + 0], kv = ctf[b * 5 + 1], cs = ctf[b * 5 + 2] * 1e7, w = ctf[b * 5 + 3],
+               apix = ctf[b * 5 + 4];
+  const double V = kv * 1e3;
+  const double lam = 12.2643 / sqrt(V * (1.0 + 0.978466e-6 * V));
+  const double s2 = 1.0 / ((double)D * apix * (double)D * apix);
+  const double alpha = lam * df * s2;
+  const double beta = 0.5 * cs * lam * lam * lam * s2 * s2;
+  const float ahi = (float)alpha;
+  cst[0] = ahi;
+  cst[1] = (float)(alpha - (double)ahi);
+  cst[2] = (float)beta;
+  cst[3] = (float)sqrt(1.0 - w * w);
+  cst[4] = (float)w;
+}
+
+// H_hat at half-spectrum element idx = l (D / 2 + 1) + m (row l, column m) of a D x D image.
+__device__ __forceinline__ float ctf_value(int idx, int D, int W2, const float cst[5]) {
+  const int l = idx / W2, m = idx - l * W2;
+  const int fy = l < (D + 1) / 2 ? l : l - D;
+  const float n = (float)(fy * fy + m * m);  // exact (< 2^24)
+  const float p = cst[0] * n;
+  const float perr = fmaf(cst[0], n, -p);        // exact remainder of alpha_hi * n
+  const float pred = p - 2.f * rintf(0.5f * p);  // exact: p mod 2 in [-1, 1]
+  const float q = cst[2] * n * n;
+  const float qred = q - 2.f * rintf(0.5f * q);
+  const float tt = (pred + perr + cst[1] * n) - qred;
+  float sp, cp;
+  sincospif(tt, &sp, &cp);
+  return -(cst[3] * sp + cst[4] * cp);
+}
+
 __global__ void k_ctf_mul(float2* __restrict__ spec, const float* __restrict__ ctf, int D) {
   const int b = blockIdx.y;
   const int W2 = D / 2 + 1;
   __shared__ float cst[6];
   if (threadIdx.x == 0) {
-    const double df = ctf[b * 5 + 0], kv = ctf[b * 5 + 1], cs = ctf[b * 5 + 2] * 1e7, w = ctf[b * 5 + 3],
-                 apix = ctf[b * 5 + 4];
-    const double V = kv * 1e3;
-    const double lam = 12.2643 / sqrt(V * (1.0 + 0.978466e-6 * V));
-    const double s2 = 1.0 / ((double)D * apix * (double)D * apix);
-    const double alpha = lam * df * s2;
-    const double beta = 0.5 * cs * lam * lam * lam * s2 * s2;
-    const float ahi = (float)alpha;
-    cst[0] = ahi;
-    cst[1] = (float)(alpha - (double)ahi);
-    cst[2] = (float)beta;
-    cst[3] = (float)sqrt(1.0 - w * w);
-    cst[4] = (float)w;
+    ctf_constants(ctf, b, D, cst);
     cst[5] = (float)(1.0 / ((double)D * (double)D));
   }
   __syncthreads();
-  const float a_hi = cst[0], a_lo = cst[1], bet = cst[2], sw = cst[3], wc = cst[4], sc = cst[5];
+  const float c[5] = {cst[0], cst[1], cst[2], cst[3], cst[4]};
+  const float sc = cst[5];
   float2* img = spec + (size_t)b * D * W2;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < D * W2; idx += gridDim.x * blockDim.x) {
-    const int l = idx / W2, m = idx - l * W2;
-    const int fy = l < (D + 1) / 2 ? l : l - D;
-    const float n = (float)(fy * fy + m * m);  // exact (< 2^24)
-    const float p = a_hi * n;
-    const float perr = fmaf(a_hi, n, -p);          // exact remainder of alpha_hi * n
-    const float pred = p - 2.f * rintf(0.5f * p);  // exact: p mod 2 in [-1, 1]
-    const float q = bet * n * n;
-    const float qred = q - 2.f * rintf(0.5f * q);
-    const float tt = (pred + perr + a_lo * n) - qred;
-    float sp, cp;
-    sincospif(tt, &sp, &cp);
-    const float H = -(sw * sp + wc * cp) * sc;
+    const float H = ctf_value(idx, D, W2, c) * sc;
     float2 v = img[idx];
     v.x *= H;
     v.y *= H;
@@ -90,6 +102,56 @@ __global__ void __cluster_dims__(kLossCtas, 1, 1) k_loss(const float* __restrict
     float v = 0.f;
     for (int r = 0; r < kLossCtas; ++r) v += *cluster.map_shared_rank(&red[0], r);
     loss[b] = v * scale;
+  }
+  cluster.sync();  // the other CTAs' shared memory stays alive until it has been read
+}
+
+// CTF, loss and adjoint CTF of one image in the Fourier domain, one cluster of kLossCtas CTAs
+// per image.  With the unnormalized R2C spectra Q_hat, Y_hat and Z = H_hat Q_hat - Y_hat (the
+// spectrum of X - Y, since H_hat is real and even), Parseval gives
+// sum (X - Y)^2 = sum over the full spectrum |Z|^2 / D^2 (half-spectrum columns other than 0
+// and D / 2 count twice), and the adjoint CTF of dL/dX = 2 s (X - Y) is
+// C2R(2 s H_hat Z) / D^2, written over Q_hat.  The loss is reduced as in k_loss.
+__global__ void __cluster_dims__(kLossCtas, 1, 1) k_ctf_loss(float2* __restrict__ specQ,
+                                                             const float2* __restrict__ specY,
+                                                             const float* __restrict__ ctf, int D, float scale,
+                                                             float* __restrict__ loss) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int b = blockIdx.y, part = (int)cluster.block_rank();
+  const int W2 = D / 2 + 1;
+  __shared__ float cst[5];
+  __shared__ float red[32];
+  if (threadIdx.x == 0) ctf_constants(ctf, b, D, cst);
+  __syncthreads();
+  const float c[5] = {cst[0], cst[1], cst[2], cst[3], cst[4]};
+  const float inv_d2 = 1.f / ((float)D * (float)D);
+  const float gscale = 2.f * scale * inv_d2;
+  float2* q = specQ + (size_t)b * D * W2;
+  const float2* y = specY + (size_t)b * D * W2;
+  float acc = 0.f;
+  for (int idx = part * blockDim.x + threadIdx.x; idx < D * W2; idx += kLossCtas * blockDim.x) {
+    const float H = ctf_value(idx, D, W2, c);
+    const float2 qv = q[idx], yv = y[idx];
+    const float zx = fmaf(H, qv.x, -yv.x), zy = fmaf(H, qv.y, -yv.y);
+    const int m = idx % W2;
+    const float wgt = (m == 0 || 2 * m == D) ? 1.f : 2.f;
+    acc = fmaf(wgt, fmaf(zx, zx, zy * zy), acc);
+    const float gH = gscale * H;
+    q[idx] = make_float2(gH * zx, gH * zy);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) red[0] = v;
+  }
+  cluster.sync();
+  if (part == 0 && threadIdx.x == 0) {
+    float v = 0.f;
+    for (int r = 0; r < kLossCtas; ++r) v += *cluster.map_shared_rank(&red[0], r);
+    loss[b] = v * inv_d2 * scale;
   }
   cluster.sync();  // the other CTAs' shared memory stays alive until it has been read
 }
@@ -188,6 +250,14 @@ cudaError_t launch_ctf_mul(const gs_config& cfg, float2* spec, const float* ctf,
   if (per_image > 8) per_image = 8;  // a few CTAs per image: few FP64 prologues
   dim3 grid(per_image, B);
   k_ctf_mul<<<grid, 256, 0, s>>>(spec, ctf, D);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ctf_loss(const gs_config& cfg, float2* specQ, const float2* specY, const float* ctf, int B,
+                            float* loss, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  const float scale = cfg.reduction == 1 ? 1.f / ((float)cfg.D * (float)cfg.D) : 1.f;
+  k_ctf_loss<<<dim3(kLossCtas, B), 256, 0, s>>>(specQ, specY, ctf, cfg.D, scale, loss);
   return cudaGetLastError();
 }
 

@@ -28,7 +28,7 @@ enum GaussField {
 
 // Workspace carve-up; every part 256-byte aligned.
 struct WsLayout {
-  size_t status, gauss, hist, tstart, ttotal, itotal, ibase, gacc, spec, fftwork, total;
+  size_t status, gauss, hist, tstart, ttotal, itotal, ibase, gacc, spec, spec2, fftwork, total;
   int Tn, C, ntx;
 };
 
@@ -50,6 +50,7 @@ inline WsLayout ws_layout(const gs_config& cfg, int B, int N, size_t fft_work) {
   L.ibase = o; o = align256(o + sizeof(unsigned long long) * ((size_t)B + 1));
   L.gacc = o; o = align256(o + sizeof(float) * kGradStride * (size_t)N);
   L.spec = o; o = align256(o + 2 * sizeof(float) * (size_t)B * cfg.D * (cfg.D / 2 + 1));
+  L.spec2 = o; o = align256(o + 2 * sizeof(float) * (size_t)B * cfg.D * (cfg.D / 2 + 1));
   L.fftwork = o; o = align256(o + fft_work);
   L.total = o;
   return L;
@@ -129,6 +130,8 @@ cudaError_t launch_render_bwd(const gs_config& cfg, const gs_record* proj, int N
 cudaError_t launch_bwd_finalize(const float* theta, const float* gauss, int N, float* gacc, float* dtheta,
                                 cudaStream_t s);
 cudaError_t launch_ctf_mul(const gs_config& cfg, float2* spec, const float* ctf, int B, cudaStream_t s);
+cudaError_t launch_ctf_loss(const gs_config& cfg, float2* specQ, const float2* specY, const float* ctf, int B,
+                            float* loss, cudaStream_t s);
 cudaError_t launch_loss(const gs_config& cfg, const float* X, const float* Y, int B, float* loss,
                         float* dLdX, cudaStream_t s);
 cudaError_t launch_adam(float* theta, const float* g, float* m, float* v, int n, float lr,

@@ -2,7 +2,8 @@
 
 ``Splatter`` owns the torch-allocated buffers that the C-ABI calls need for a fixed
 (D, N, B) and runs the path: gs_project -> gs_bin_sort -> gs_render_fwd -> gs_apply_ctf ->
-gs_loss -> gs_apply_ctf (adjoint) -> gs_render_bwd -> gs_step.  Every step runs in libgs;
+gs_loss -> gs_apply_ctf (adjoint) -> gs_render_bwd -> gs_step, or with the three middle steps
+fused into gs_ctf_loss_grad.  Every step runs in libgs;
 this module only allocates and sequences.
 """
 from __future__ import annotations
@@ -95,6 +96,12 @@ class Splatter:
         L.gs_loss(self.cfg, X, Y, self.loss, self.dX)
         return self.loss[: self.B], self.dX
 
+    def ctf_loss_grad(self, Q, ctf, Y):
+        """Loss and dL/dQ (into self.dQ) through CTF, loss and adjoint CTF in one call
+        (Parseval in the Fourier domain); X is not formed."""
+        L.gs_ctf_loss_grad(self.cfg, Q, Y, ctf, self.loss, self.dQ, self.fft, self.ws)
+        return self.loss[: self.B], self.dQ
+
     def backward(self, theta, W, dQ, dtheta, dpose=None):
         """Accumulates dL/dtheta into dtheta; with ``dpose`` ([B, 12], zeroed by the caller)
         also dL/dW (dpose[:, 0:9], row-major) and dL/dt (dpose[:, 10:12])."""
@@ -118,11 +125,17 @@ class Splatter:
             return self.Q, self.X
         return self.Q, None
 
-    def forward_backward(self, theta, W, ctf, Y, dtheta, grow=True):
+    def forward_backward(self, theta, W, ctf, Y, dtheta, grow=True, fused=False):
         """One fwd+CTF+loss+bwd pass; accumulates dL/dtheta into dtheta (caller zeroes it).
-        Returns the per-image losses (device tensor)."""
-        self.forward(theta, W, ctf, grow)
-        self.loss_grad(self.X, Y)
-        self.apply_ctf(self.dX, ctf, self.dQ)
+        Returns the per-image losses (device tensor).  fused: CTF, loss and adjoint CTF in
+        one call that does not form X (as a training step runs them); otherwise X and dL/dX
+        are left in self.X and self.dX."""
+        if fused:
+            self.forward(theta, W, None, grow)
+            self.ctf_loss_grad(self.Q, ctf, Y)
+        else:
+            self.forward(theta, W, ctf, grow)
+            self.loss_grad(self.X, Y)
+            self.apply_ctf(self.dX, ctf, self.dQ)
         self.backward(theta, W, self.dQ, dtheta)
         return self.loss[: self.B]

@@ -46,7 +46,7 @@ def _eager(D, host, tile=16, chunk=64):
     t = torch.from_numpy(th).cuda()
     g = torch.zeros_like(t)
     loss = sp.forward_backward(t, torch.from_numpy(Ws.reshape(B, 9)).cuda(), torch.from_numpy(ctf).cuda(),
-                               torch.from_numpy(Y).cuda(), g)
+                               torch.from_numpy(Y).cuda(), g, fused=True)
     out = loss.cpu().numpy(), g.cpu().numpy()
     sp.close()
     return out
@@ -94,10 +94,10 @@ def test_replay_with_new_inputs_and_counted_adam():
     t = th0.clone()
     m, v, g = torch.zeros_like(t), torch.zeros_like(t), torch.zeros_like(t)
     W1, C1, Y1 = (torch.from_numpy(x).cuda() for x in (host[1].reshape(4, 9), host[2], host[3]))
-    e1 = sp.forward_backward(t, W1, C1, Y1, g).cpu().numpy()
+    e1 = sp.forward_backward(t, W1, C1, Y1, g, fused=True).cpu().numpy()
     L.gs_step(t, g, m, v, 1)
     g.zero_()
-    e2 = sp.forward_backward(t, W2, C2, Y2, g).cpu().numpy()
+    e2 = sp.forward_backward(t, W2, C2, Y2, g, fused=True).cpu().numpy()
     L.gs_step(t, g, m, v, 2)
     torch.cuda.synchronize()
     assert np.allclose(l1, e1, rtol=1e-6) and np.allclose(l2, e2, rtol=1e-5)

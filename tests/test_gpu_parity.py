@@ -161,6 +161,39 @@ def test_mean_reduction(c1):
         assert rel_l2(out["dtheta"][:, sl], ref["dtheta"][:, sl]) < 1e-3, name
 
 
+@pytest.mark.parametrize("D,reduction", [(64, 0), (33, 0), (40, 1)])
+def test_fused_ctf_loss_grad_matches_oracle(D, reduction):
+    """gs_ctf_loss_grad (CTF, loss and adjoint CTF by Parseval in the Fourier domain) gives
+    the oracle's loss and dL/dQ, and the unfused calls' values; dLdQ may alias Q."""
+    th, Ws, ctf, Y = make_batch(80 + D, D, 600, 5)
+    ref = O.forward_backward(th, Ws, D, Y, ctf, reduction=reduction)
+    N, B = th.shape[0], Ws.shape[0]
+    sp = Splatter(D, N, B, tile=8, chunk=64, reduction=reduction)
+    t, W, c, y = to_dev(th, Ws.reshape(B, 9), ctf, Y)
+    dth = torch.zeros_like(t)
+    loss = sp.forward_backward(t, W, c, y, dth, fused=True).cpu().numpy()
+    dQ = sp.dQ.cpu().numpy()
+    assert np.allclose(loss, ref["L"], rtol=1e-5, atol=0)
+    for b in range(B):
+        assert rel_l2(dQ[b], ref["dLdQ"][b]) < 1e-5
+    g = dth.cpu().numpy()
+    for name, sl in GROUPS:
+        assert rel_l2(g[:, sl], ref["dtheta"][:, sl]) < 1e-3, name
+    # the unfused calls on the same Q
+    sp.apply_ctf(sp.Q, c, sp.X)
+    l2, _ = sp.loss_grad(sp.X, y)
+    sp.apply_ctf(sp.dX, c, sp.X)
+    assert np.allclose(loss, l2.cpu().numpy(), rtol=2e-6)
+    assert rel_l2(dQ, sp.X.cpu().numpy()) < 2e-6
+    # in place: dLdQ written over Q
+    Qc = sp.Q.clone()
+    l3 = torch.empty(B, device=DEV)
+    L.gs_ctf_loss_grad(sp.cfg, Qc, y, c, l3, Qc, sp.fft, sp.ws)
+    torch.cuda.synchronize()
+    assert torch.equal(Qc, sp.dQ) and np.array_equal(l3.cpu().numpy(), loss)
+    sp.close()
+
+
 def test_adam_step_matches_oracle():
     rng = synth.rng_for(5)
     th = rng.standard_normal(11 * 500).astype(np.float32)
