@@ -44,9 +44,9 @@ CTF_SNR = 0.05
 # each render kernel, from the capture summarised in profiles/render_kernels_d256_n100k_b64.md
 # (B = 64; the kernels read each pair's index and record once, so traffic scales with the pair
 # count).  Valid only for the gs_render.cu whose SHA-256 is recorded: otherwise null.
-RENDER_TRAFFIC = {"sha256": "7d3d3b528c2977c083654718e1b99c77b72ff17497c526e311ff2a54e3ded674",
-                  "bytes_per_pair": {"fwd": (306.622720e6 + 16.562944e6) / 25319264,
-                                     "bwd": (320.568832e6 + 3.189760e6) / 25319264}}
+RENDER_TRAFFIC = {"sha256": "32d116bf69feb054c6fc50db367bf0c5b6b49a2a9dbc62d625825af0ffbe4b10",
+                  "bytes_per_pair": {"fwd": (306.626560e6 + 16.540160e6) / 25319264,
+                                     "bwd": (320.808448e6 + 3.612928e6) / 25319264}}
 
 
 # libgs kernels launched by one graph-captured training step (cuFFT's and torch's gradient
