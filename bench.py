@@ -451,25 +451,34 @@ def main():
     Yh = Y.cpu().pin_memory()
     Wh = W.cpu().pin_memory()
     Ch = C.cpu().pin_memory()
-    lossh = torch.empty(args.B, dtype=torch.float32).pin_memory()
+    lossh = [torch.empty(args.B, dtype=torch.float32).pin_memory() for _ in range(2)]
     h2d = Yh.numel() * 4 + Wh.numel() * 4 + Ch.numel() * 4
-    d2h = lossh.numel() * 4
+    d2h = lossh[0].numel() * 4
     # every step copies its own inputs from pinned host memory (double-buffered: the next
     # step's copy overlaps the current step) and reads its per-image losses back to the host
     from paper_2508_04929_b300.batched import HostFeeder
     feeder = HostFeeder(gs)
-    done = torch.cuda.Event()
+    done = [torch.cuda.Event(), torch.cuda.Event()]
+    host_losses = 0.0
     torch.cuda.synchronize()
     s0 = time.perf_counter()
     feeder.prefetch(Wh, Ch, Yh)
+    # each step's losses come back to pinned host memory; the host reads them one step later,
+    # after enqueueing the next step, so that the GPU never waits for the host
+    pending = None
     for i in range(args.steps):
         feeder.load()
         if i + 1 < args.steps:
             feeder.prefetch(Wh, Ch, Yh)
         step()
-        lossh.copy_(prob.sp.loss[: args.B], non_blocking=True)
-        done.record()
-        done.synchronize()  # the host has this step's losses
+        lossh[i % 2].copy_(prob.sp.loss[: args.B], non_blocking=True)
+        done[i % 2].record()
+        if pending is not None:
+            done[pending].synchronize()  # the host has the previous step's losses
+            host_losses += float(lossh[pending].sum())
+        pending = i % 2
+    done[pending].synchronize()
+    host_losses += float(lossh[pending].sum())
     e2e = world * args.B * args.steps / (time.perf_counter() - s0)
     torch.cuda.synchronize()
     gs.close()
@@ -507,7 +516,7 @@ def main():
             "plain_form": {"value": plain, "unit": UNIT, "form": "one particle per launch sequence, Adam per image"},
             "speedup_vs_plain": (value / world / plain) if plain else None,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "pipelining": "next step's host->device copy overlaps the current step; losses read back every step"},
+                    "pipelining": "next step's host->device copy overlaps the current step; every step's losses are copied back and read by the host one step later"},
             "gpu_launches": len(STEP_KERNELS) * args.steps,
             "roofline": {"bound": "alu", "kernel": f"k_render_{dom}", "achieved": achieved / 1e9,
                          "peak": peak_exp / 1e9, "unit": "Gex2/s", "frac": achieved / peak_exp,
