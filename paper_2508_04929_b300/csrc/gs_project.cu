@@ -89,6 +89,15 @@ __global__ void k_activate(const float* __restrict__ theta, int N, float* __rest
 
 constexpr int kProjParticles = 4;  // particles per thread: one load of the Gaussian's row serves them all
 
+// One 32-byte store: the record fills its sector in a single request (proj 32-byte aligned).
+__device__ __forceinline__ void st_record32(gs_record* dst, const gs_record& r) {
+  const float* f = reinterpret_cast<const float*>(&r);
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(dst), "f"(f[0]), "f"(f[1]),
+               "f"(f[2]), "f"(f[3]), "f"(f[4]), "f"(f[5]), "f"(f[6]), "f"(f[7])
+               : "memory");
+}
+
+template <bool kV8>
 __global__ void k_project(const float* __restrict__ gauss, int N, const float* __restrict__ Wall, int B, int D,
                           float inv_h, float kcut, gs_record* __restrict__ proj, int2* __restrict__ boxes,
                           int* __restrict__ status) {
@@ -171,10 +180,14 @@ __global__ void k_project(const float* __restrict__ gauss, int N, const float* _
       }
     }
     any_bad |= bad;
-    float4* dst = reinterpret_cast<float4*>(proj + (size_t)b * N + g);
-    const float4* srcp = reinterpret_cast<const float4*>(&r);
-    dst[0] = srcp[0];
-    dst[1] = srcp[1];
+    if (kV8) {
+      st_record32(proj + (size_t)b * N + g, r);
+    } else {
+      float4* dst = reinterpret_cast<float4*>(proj + (size_t)b * N + g);
+      const float4* srcp = reinterpret_cast<const float4*>(&r);
+      dst[0] = srcp[0];
+      dst[1] = srcp[1];
+    }
     // the box again in the plane after the records, for the binning passes
     boxes[(size_t)b * N + g] = make_int2((int)(((unsigned)(uint16_t)r.x0) | ((unsigned)(uint16_t)r.x1 << 16)),
                                          (int)(((unsigned)(uint16_t)r.y0) | ((unsigned)(uint16_t)r.y1 << 16)));
@@ -195,7 +208,10 @@ cudaError_t launch_project(const gs_config& cfg, const float* gauss, int N, cons
   if (N <= 0 || B <= 0) return cudaSuccess;
   dim3 grid((N + 255) / 256, (B + kProjParticles - 1) / kProjParticles);
   int2* boxes = reinterpret_cast<int2*>(proj + (size_t)B * N);  // box plane after the B * N records
-  k_project<<<grid, 256, 0, s>>>(gauss, N, W, B, cfg.D, inv_pixel(cfg), cfg.cutoff_sigma, proj, boxes, status);
+  if ((reinterpret_cast<uintptr_t>(proj) & 31) == 0)
+    k_project<true><<<grid, 256, 0, s>>>(gauss, N, W, B, cfg.D, inv_pixel(cfg), cfg.cutoff_sigma, proj, boxes, status);
+  else
+    k_project<false><<<grid, 256, 0, s>>>(gauss, N, W, B, cfg.D, inv_pixel(cfg), cfg.cutoff_sigma, proj, boxes, status);
   return cudaGetLastError();
 }
 
