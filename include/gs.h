@@ -80,11 +80,13 @@ typedef struct gs_record {
 
 /* Opaque pair of batched cuFFT plans (R2C and C2R over B images of D x D). */
 typedef struct gs_fft {
-  int r2c;           /* cufftHandle */
-  int c2r;           /* cufftHandle */
+  int r2c;           /* cufftHandle: 2-D R2C over B images */
+  int c2r;           /* cufftHandle: 2-D C2R over B images */
   int D;
   int B;
   size_t work_bytes; /* cuFFT work area needed (placed inside the gs workspace) */
+  int r2c_rows;      /* cufftHandle: 1-D R2C of the B * D rows (D = 256 only, else 0) */
+  int c2r_rows;      /* cufftHandle: 1-D C2R of the B * D rows (D = 256 only, else 0) */
 } gs_fft;
 
 /* ---------------------------------------------------------------------------------------
@@ -191,7 +193,9 @@ int gs_loss(const gs_config* cfg, const float* X, const float* Y, int B, float* 
  * |Z|^2 / D^2 (s = 1 for reduction 0, 1 / D^2 for reduction 1), and
  * dLdQ = C2R(2 s H_hat Z) / D^2 is the adjoint CTF of dL/dX = 2 s (X - Y): the values of
  * gs_apply_ctf + gs_loss + gs_apply_ctf up to FP32 rounding, with three FFTs instead of
- * four.  Q, Y, dLdQ [B * D * D]; ctf as for gs_apply_ctf; dLdQ may alias Q.  Uses cuFFT
+ * four.  For D = 256 the 2-D transforms are split: cuFFT transforms the rows, and one kernel
+ * runs the column FFTs of Q and Y, the pointwise step and the inverse column FFT together
+ * (four passes over the spectra instead of seven).  Q, Y, dLdQ [B * D * D]; ctf as for gs_apply_ctf; dLdQ may alias Q.  Uses cuFFT
  * (fft created for this D and B) and two half spectra plus the work area at the tail of
  * ws (gs_workspace_size includes them). */
 int gs_ctf_loss_grad(const gs_config* cfg, const float* Q, const float* Y, const float* ctf, int B,

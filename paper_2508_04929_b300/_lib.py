@@ -35,7 +35,7 @@ class GsConfig(ctypes.Structure):
 
 class GsFFT(ctypes.Structure):
     _fields_ = [("r2c", ctypes.c_int), ("c2r", ctypes.c_int), ("D", ctypes.c_int), ("B", ctypes.c_int),
-                ("work_bytes", ctypes.c_size_t)]
+                ("work_bytes", ctypes.c_size_t), ("r2c_rows", ctypes.c_int), ("c2r_rows", ctypes.c_int)]
 
 
 class GsFSC(ctypes.Structure):

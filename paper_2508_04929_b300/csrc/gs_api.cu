@@ -58,7 +58,7 @@ int gs_workspace_size(const gs_config* cfg, int B, int N, size_t fft_work_bytes,
 
 int gs_fft_create(int D, int B, gs_fft* fft) {
   if (!fft || D < 1 || D > 4096 || B < 1) return GS_EINVAL;
-  fft->r2c = fft->c2r = 0;
+  fft->r2c = fft->c2r = fft->r2c_rows = fft->c2r_rows = 0;
   fft->D = D;
   fft->B = B;
   fft->work_bytes = 0;
@@ -80,6 +80,28 @@ int gs_fft_create(int D, int B, gs_fft* fft) {
   fft->r2c = (int)a;
   fft->c2r = (int)c;
   fft->work_bytes = wa > wc ? wa : wc;
+  if (D == 256) {  // row transforms for the column kernel of gs_ctf_loss_grad
+    cufftHandle ar, cr;
+    if (cufftCreate(&ar) != CUFFT_SUCCESS) { gs_fft_destroy(fft); return GS_ECUDA; }
+    if (cufftCreate(&cr) != CUFFT_SUCCESS) { cufftDestroy(ar); gs_fft_destroy(fft); return GS_ECUDA; }
+    cufftSetAutoAllocation(ar, 0);
+    cufftSetAutoAllocation(cr, 0);
+    int n1[1] = {D};
+    size_t war = 0, wcr = 0;
+    if (cufftMakePlanMany(ar, 1, n1, nullptr, 1, D, nullptr, 1, D / 2 + 1, CUFFT_R2C, B * D, &war) !=
+            CUFFT_SUCCESS ||
+        cufftMakePlanMany(cr, 1, n1, nullptr, 1, D / 2 + 1, nullptr, 1, D, CUFFT_C2R, B * D, &wcr) !=
+            CUFFT_SUCCESS) {
+      cufftDestroy(ar);
+      cufftDestroy(cr);
+      gs_fft_destroy(fft);
+      return GS_ECUDA;
+    }
+    fft->r2c_rows = (int)ar;
+    fft->c2r_rows = (int)cr;
+    if (war > fft->work_bytes) fft->work_bytes = war;
+    if (wcr > fft->work_bytes) fft->work_bytes = wcr;
+  }
   return GS_OK;
 }
 
@@ -87,7 +109,9 @@ int gs_fft_destroy(gs_fft* fft) {
   if (!fft) return GS_EINVAL;
   if (fft->r2c) cufftDestroy((cufftHandle)fft->r2c);
   if (fft->c2r) cufftDestroy((cufftHandle)fft->c2r);
-  fft->r2c = fft->c2r = 0;
+  if (fft->r2c_rows) cufftDestroy((cufftHandle)fft->r2c_rows);
+  if (fft->c2r_rows) cufftDestroy((cufftHandle)fft->c2r_rows);
+  fft->r2c = fft->c2r = fft->r2c_rows = fft->c2r_rows = 0;
   return GS_OK;
 }
 
@@ -177,15 +201,32 @@ int gs_ctf_loss_grad(const gs_config* cfg, const float* Q, const float* Y, const
   if (B == 0) return GS_OK;
   if (!Q || !Y || !ctf || !loss || !dLdQ || !fft || !ws || !aligned(ws, 256)) return GS_EINVAL;
   if (fft->D != cfg->D || fft->B != B) return GS_EINVAL;
-  // two half spectra and the cuFFT work area at the tail of the workspace
+  // two half spectra, the cuFFT work area and the loss partial sums at the tail of the workspace
   cudaStream_t s = (cudaStream_t)stream;
   const size_t spec_bytes = align256(2 * sizeof(float) * (size_t)B * cfg->D * (cfg->D / 2 + 1));
-  const size_t need = 2 * spec_bytes + align256(fft->work_bytes);
+  const size_t work_bytes = align256(fft->work_bytes);
+  const size_t need = 2 * spec_bytes + work_bytes + ctf_cols_red_bytes(B);
   if (ws_bytes < need) return GS_ENOSPC;
   const size_t off = (ws_bytes - need) & ~size_t(255);
   float2* specY = ws_ptr<float2>(ws, off);
   float2* specQ = ws_ptr<float2>(ws, off + spec_bytes);
   void* work = ws_ptr<void>(ws, off + 2 * spec_bytes);
+  if (cfg->D == 256 && fft->r2c_rows && fft->c2r_rows) {
+    // rows by cuFFT; column FFTs, the pointwise step and the inverse column FFT in one kernel
+    cufftHandle ar = (cufftHandle)fft->r2c_rows, cr = (cufftHandle)fft->c2r_rows;
+    if (cufftSetStream(ar, s) != CUFFT_SUCCESS || cufftSetStream(cr, s) != CUFFT_SUCCESS) return GS_ECUDA;
+    if (cufftSetWorkArea(ar, work) != CUFFT_SUCCESS || cufftSetWorkArea(cr, work) != CUFFT_SUCCESS)
+      return GS_ECUDA;
+    if (cufftExecR2C(ar, const_cast<float*>(Q), reinterpret_cast<cufftComplex*>(specQ)) != CUFFT_SUCCESS)
+      return GS_ECUDA;
+    if (cufftExecR2C(ar, const_cast<float*>(Y), reinterpret_cast<cufftComplex*>(specY)) != CUFFT_SUCCESS)
+      return GS_ECUDA;
+    if (launch_ctf_cols(*cfg, specQ, specY, ctf, B, loss, ws_ptr<void>(ws, off + 2 * spec_bytes + work_bytes), s) !=
+        cudaSuccess)
+      return GS_ECUDA;
+    if (cufftExecC2R(cr, reinterpret_cast<cufftComplex*>(specQ), dLdQ) != CUFFT_SUCCESS) return GS_ECUDA;
+    return GS_OK;
+  }
   cufftHandle a = (cufftHandle)fft->r2c, c = (cufftHandle)fft->c2r;
   if (cufftSetStream(a, s) != CUFFT_SUCCESS || cufftSetStream(c, s) != CUFFT_SUCCESS) return GS_ECUDA;
   if (cufftSetWorkArea(a, work) != CUFFT_SUCCESS || cufftSetWorkArea(c, work) != CUFFT_SUCCESS) return GS_ECUDA;

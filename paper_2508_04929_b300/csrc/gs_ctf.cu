@@ -156,6 +156,163 @@ __global__ void __cluster_dims__(kLossCtas, 1, 1) k_ctf_loss(float2* __restrict_
   cluster.sync();  // the other CTAs' shared memory stays alive until it has been read
 }
 
+// ---------------------------------------------------------------------------------------
+// CTF, loss and adjoint CTF for D = 256 on row-transformed spectra (the column half of the
+// 2-D transforms, the pointwise step and the inverse column transforms in one pass).
+// qr, yr [B][256][129]: the 1-D R2C transforms of the rows of Q and Y.  One CTA owns 16
+// columns kx of one image: it runs the forward 256-point FFT along y of both (y = 16 a + b,
+// k = c + 16 d: a 16-point DFT over a, twiddle w256^(b c), a 16-point DFT over b; each
+// 16-point DFT is 4 x 4 in registers), forms Z = H Q_hat - Y_hat, the loss terms and
+// G = 2 s H Z / D^2, and runs the inverse FFT of G along y, written over qr for the row C2R.
+// Each CTA adds its loss terms in a fixed order; the image's last CTA (a ticket counter)
+// adds the CTAs' sums in index order.
+// ---------------------------------------------------------------------------------------
+constexpr int kColD = 256, kColW2 = kColD / 2 + 1, kColNC = 16;
+static_assert(kColCtas == (kColW2 + kColNC - 1) / kColNC, "CTAs per image of k_ctf_cols");
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+
+// 4-point DFT in place, X_k = sum_m x_m w^(m k), w = exp(-2 pi i / 4) (kInv: the conjugate).
+template <bool kInv>
+__device__ __forceinline__ void dft4(float2& a, float2& b, float2& c, float2& d) {
+  const float2 s0 = cadd(a, c), s1 = csub(a, c), s2 = cadd(b, d), bd = csub(b, d);
+  const float2 s3 = kInv ? make_float2(-bd.y, bd.x) : make_float2(bd.y, -bd.x);  // w (b - d)
+  a = cadd(s0, s2);
+  c = csub(s0, s2);
+  b = cadd(s1, s3);
+  d = csub(s1, s3);
+}
+
+// 16-point DFT of x[0..15] (x[n] at position n): X[k1 + 4 k2] ends at position 4 k1 + k2.
+template <bool kInv>
+__device__ __forceinline__ void dft16(float2 (&x)[16]) {
+#pragma unroll
+  for (int l = 0; l < 4; ++l) dft4<kInv>(x[l], x[4 + l], x[8 + l], x[12 + l]);  // over m, x[4 m + l]
+  // twiddles w16^(l k1) at position 4 k1 + l (cos, sin of 2 pi j / 16)
+  const float c1 = 0.92387953251128674f, s1 = 0.38268343236508978f, h = 0.70710678118654752f;
+  const float2 w1 = make_float2(c1, kInv ? s1 : -s1), w2 = make_float2(h, kInv ? h : -h),
+               w3 = make_float2(s1, kInv ? c1 : -c1), w6 = make_float2(-h, kInv ? h : -h),
+               w9 = make_float2(-c1, kInv ? -s1 : s1);
+  x[5] = cmul(x[5], w1);    // l 1, k1 1
+  x[6] = cmul(x[6], w2);    // l 2, k1 1
+  x[7] = cmul(x[7], w3);    // l 3, k1 1
+  x[9] = cmul(x[9], w2);    // l 1, k1 2
+  x[10] = kInv ? make_float2(-x[10].y, x[10].x) : make_float2(x[10].y, -x[10].x);  // w16^4
+  x[11] = cmul(x[11], w6);  // l 3, k1 2
+  x[13] = cmul(x[13], w3);  // l 1, k1 3
+  x[14] = cmul(x[14], w6);  // l 2, k1 3
+  x[15] = cmul(x[15], w9);  // l 3, k1 3
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft4<kInv>(x[4 * k1], x[4 * k1 + 1], x[4 * k1 + 2], x[4 * k1 + 3]);
+}
+
+// 256-point FFT along the rows of a [256][16] shared array, one column per 16 threads
+// (thread: column j = t & 15, sub = t >> 4).  tw[m] = w256^m; kInv uses the conjugates.
+template <bool kInv>
+__device__ __forceinline__ void fft256_cols(float2* __restrict__ a, const float2* __restrict__ tw) {
+  const int j = threadIdx.x & 15, sub = threadIdx.x >> 4;
+  float2 x[16];
+  // step 1 (this thread's fine index b = sub): a 16-point DFT over the coarse index, twiddled
+#pragma unroll
+  for (int n = 0; n < 16; ++n) x[n] = a[(16 * n + sub) * kColNC + j];
+  dft16<kInv>(x);
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    float2 v = x[4 * (c & 3) + (c >> 2)];
+    if (c != 0) v = cmul(v, kInv ? conjf2(tw[sub * c]) : tw[sub * c]);
+    a[(16 * c + sub) * kColNC + j] = v;
+  }
+  __syncthreads();
+  // step 2 (this thread's c = sub): a 16-point DFT over the fine index
+#pragma unroll
+  for (int n = 0; n < 16; ++n) x[n] = a[(16 * sub + n) * kColNC + j];
+  __syncthreads();
+  dft16<kInv>(x);
+#pragma unroll
+  for (int d = 0; d < 16; ++d) a[(sub + 16 * d) * kColNC + j] = x[4 * (d & 3) + (d >> 2)];
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_ctf_cols(float2* __restrict__ qr, const float2* __restrict__ yr,
+                                                  const float* __restrict__ ctf, float scale,
+                                                  float* __restrict__ partial, unsigned* __restrict__ ticket,
+                                                  float* __restrict__ loss) {
+  extern __shared__ float2 csm[];
+  float2* aq = csm;                      // [256][16]
+  float2* ay = csm + kColD * kColNC;     // [256][16]
+  float2* tw = csm + 2 * kColD * kColNC; // [256]
+  __shared__ float cst[5];
+  __shared__ float red[8];
+  __shared__ bool last;
+  const int b = blockIdx.y, c0 = blockIdx.x * kColNC;
+  const int j = threadIdx.x & 15, sub = threadIdx.x >> 4;
+  const bool col = c0 + j < kColW2;
+  if (threadIdx.x == 0) ctf_constants(ctf, b, kColD, cst);
+  {
+    float sn, cs;
+    sincospif((float)threadIdx.x / 128.f, &sn, &cs);  // w256^m = exp(-2 pi i m / 256)
+    tw[threadIdx.x] = make_float2(cs, -sn);
+  }
+  const size_t img = (size_t)b * kColD * kColW2;
+#pragma unroll 4
+  for (int r = 0; r < 16; ++r) {
+    const int y = sub + 16 * r;
+    const size_t gi = img + (size_t)y * kColW2 + c0 + j;
+    aq[y * kColNC + j] = col ? qr[gi] : make_float2(0.f, 0.f);
+    ay[y * kColNC + j] = col ? yr[gi] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  fft256_cols<false>(aq, tw);
+  fft256_cols<false>(ay, tw);
+  const float c[5] = {cst[0], cst[1], cst[2], cst[3], cst[4]};
+  const float inv_d2 = 1.f / ((float)kColD * (float)kColD);
+  const float gscale = 2.f * scale * inv_d2;
+  const int kx = c0 + j;
+  const float wgt = (kx == 0 || 2 * kx == kColD) ? 1.f : 2.f;
+  float acc = 0.f;
+#pragma unroll 4
+  for (int r = 0; r < 16; ++r) {
+    const int ky = sub + 16 * r;
+    const float H = ctf_value(ky * kColW2 + kx, kColD, kColW2, c);
+    const float2 qv = aq[ky * kColNC + j], yv = ay[ky * kColNC + j];
+    const float zx = fmaf(H, qv.x, -yv.x), zy = fmaf(H, qv.y, -yv.y);
+    if (col) acc = fmaf(wgt, fmaf(zx, zx, zy * zy), acc);
+    const float gH = gscale * H;
+    aq[ky * kColNC + j] = make_float2(gH * zx, gH * zy);
+  }
+  __syncthreads();
+  fft256_cols<true>(aq, tw);
+#pragma unroll 4
+  for (int r = 0; r < 16; ++r) {
+    const int y = sub + 16 * r;
+    if (col) qr[img + (size_t)y * kColW2 + c0 + j] = aq[y * kColNC + j];
+  }
+  // loss: this CTA's sum, then the image's last CTA adds the CTAs' sums in order
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float v = 0.f;
+    for (int w = 0; w < 8; ++w) v += red[w];
+    partial[b * kColCtas + blockIdx.x] = v;
+    __threadfence();
+    last = atomicAdd(&ticket[b], 1u) == (unsigned)(kColCtas - 1);
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    float v = 0.f;
+    for (int k = 0; k < kColCtas; ++k) v += __ldcg(&partial[b * kColCtas + k]);
+    loss[b] = v * inv_d2 * scale;
+    ticket[b] = 0u;
+  }
+}
+
 // One Adam update (Sec. 4.1; bias corrections c1 = 1 / (1 - b1^t), c2 = 1 / (1 - b2^t)).
 __device__ __forceinline__ void adam_one(float& th, float g, float& m, float& v, float lr, float b1, float b2,
                                          float eps, float c1, float c2) {
@@ -258,6 +415,22 @@ cudaError_t launch_ctf_loss(const gs_config& cfg, float2* specQ, const float2* s
   if (B <= 0) return cudaSuccess;
   const float scale = cfg.reduction == 1 ? 1.f / ((float)cfg.D * (float)cfg.D) : 1.f;
   k_ctf_loss<<<dim3(kLossCtas, B), 256, 0, s>>>(specQ, specY, ctf, cfg.D, scale, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ctf_cols(const gs_config& cfg, float2* qr, const float2* yr, const float* ctf, int B,
+                            float* loss, void* red, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  float* partial = static_cast<float*>(red);
+  unsigned* ticket = reinterpret_cast<unsigned*>(static_cast<char*>(red) + align256(sizeof(float) * (size_t)B * kColCtas));
+  cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned) * (size_t)B, s);
+  if (e != cudaSuccess) return e;
+  const size_t sm = sizeof(float2) * (2 * kColD * kColNC + kColD);
+  static int cache[64] = {0};
+  e = ensure_smem((const void*)k_ctf_cols, sm, cache);
+  if (e != cudaSuccess) return e;
+  const float scale = cfg.reduction == 1 ? 1.f / ((float)cfg.D * (float)cfg.D) : 1.f;
+  k_ctf_cols<<<dim3(kColCtas, B), 256, sm, s>>>(qr, yr, ctf, scale, partial, ticket, loss);
   return cudaGetLastError();
 }
 

@@ -28,11 +28,18 @@ enum GaussField {
 
 // Workspace carve-up; every part 256-byte aligned.
 struct WsLayout {
-  size_t status, gauss, hist, tstart, ttotal, itotal, ibase, gacc, spec, spec2, fftwork, total;
+  size_t status, gauss, hist, tstart, ttotal, itotal, ibase, gacc, spec, spec2, fftwork, red, total;
   int Tn, C, ntx;
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// CTAs per image of the D = 256 column kernel of gs_ctf_loss_grad (16 of the 129 columns
+// each) and the bytes of its loss partial sums and per-image tickets.
+constexpr int kColCtas = 9;
+inline size_t ctf_cols_red_bytes(int B) {
+  return align256(sizeof(float) * (size_t)B * kColCtas) + align256(sizeof(unsigned) * (size_t)B);
+}
 
 inline WsLayout ws_layout(const gs_config& cfg, int B, int N, size_t fft_work) {
   WsLayout L;
@@ -52,6 +59,7 @@ inline WsLayout ws_layout(const gs_config& cfg, int B, int N, size_t fft_work) {
   L.spec = o; o = align256(o + 2 * sizeof(float) * (size_t)B * cfg.D * (cfg.D / 2 + 1));
   L.spec2 = o; o = align256(o + 2 * sizeof(float) * (size_t)B * cfg.D * (cfg.D / 2 + 1));
   L.fftwork = o; o = align256(o + fft_work);
+  L.red = o; o += ctf_cols_red_bytes(B);
   L.total = o;
   return L;
 }
@@ -130,6 +138,8 @@ cudaError_t launch_render_bwd(const gs_config& cfg, const gs_record* proj, int N
 cudaError_t launch_bwd_finalize(const float* theta, const float* gauss, int N, float* gacc, float* dtheta,
                                 cudaStream_t s);
 cudaError_t launch_ctf_mul(const gs_config& cfg, float2* spec, const float* ctf, int B, cudaStream_t s);
+cudaError_t launch_ctf_cols(const gs_config& cfg, float2* qr, const float2* yr, const float* ctf, int B,
+                            float* loss, void* red, cudaStream_t s);
 cudaError_t launch_ctf_loss(const gs_config& cfg, float2* specQ, const float2* specY, const float* ctf, int B,
                             float* loss, cudaStream_t s);
 cudaError_t launch_loss(const gs_config& cfg, const float* X, const float* Y, int B, float* loss,

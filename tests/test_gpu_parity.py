@@ -161,10 +161,11 @@ def test_mean_reduction(c1):
         assert rel_l2(out["dtheta"][:, sl], ref["dtheta"][:, sl]) < 1e-3, name
 
 
-@pytest.mark.parametrize("D,reduction", [(64, 0), (33, 0), (40, 1)])
+@pytest.mark.parametrize("D,reduction", [(64, 0), (33, 0), (40, 1), (256, 0), (256, 1)])
 def test_fused_ctf_loss_grad_matches_oracle(D, reduction):
     """gs_ctf_loss_grad (CTF, loss and adjoint CTF by Parseval in the Fourier domain) gives
-    the oracle's loss and dL/dQ, and the unfused calls' values; dLdQ may alias Q."""
+    the oracle's loss and dL/dQ, and the unfused calls' values; dLdQ may alias Q.  D = 256
+    takes the row-transform + column-kernel path, the other sizes the 2-D transforms."""
     th, Ws, ctf, Y = make_batch(80 + D, D, 600, 5)
     ref = O.forward_backward(th, Ws, D, Y, ctf, reduction=reduction)
     N, B = th.shape[0], Ws.shape[0]
