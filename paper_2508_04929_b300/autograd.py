@@ -7,6 +7,8 @@ in the backward pass, recomputes each chunk's projection and per-tile Gaussian l
 the memory held across the two passes is theta, W and Q only, whatever the batch size.
 ``apply_ctf`` (self-adjoint, so its backward is itself) and ``loss`` complete the image
 formation model X = F^-1(H F Q), L = ||X - Y||^2 (App. A.2 Eq. 14, Sec. 3.3.5).
+``ctf_loss`` is the two in one call (gs_ctf_loss_grad): it returns the loss and keeps dL/dQ
+from its forward pass, without forming X.
 """
 from __future__ import annotations
 
@@ -60,6 +62,18 @@ class RenderEngine:
             sp.apply_ctf(inp[b0:b1].contiguous(), ctf[b0:b1].contiguous(), out[b0:b1])
         return out
 
+    def ctf_loss(self, Q, ctf, Y):
+        """Per-image loss of X = CTF(Q) against Y and dL/dQ, by chunks (gs_ctf_loss_grad)."""
+        B = Q.shape[0]
+        loss = torch.empty(B, dtype=torch.float32, device=Q.device)
+        dQ = torch.empty_like(Q)
+        for b0, b1 in self._chunks(B):
+            sp = self._splatter(b1 - b0)
+            lo, g = sp.ctf_loss_grad(Q[b0:b1].contiguous(), ctf[b0:b1].contiguous(), Y[b0:b1].contiguous())
+            loss[b0:b1] = lo
+            dQ[b0:b1] = g
+        return loss, dQ
+
     def close(self):
         for sp in self._sp.values():
             sp.close()
@@ -108,6 +122,19 @@ class _Loss(torch.autograd.Function):
         return dX * dloss.view(-1, 1, 1), None, None
 
 
+class _CTFLoss(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, Q, ctf, Y, engine):
+        loss, dQ = engine.ctf_loss(Q.contiguous(), ctf, Y)
+        ctx.save_for_backward(dQ)
+        return loss
+
+    @staticmethod
+    def backward(ctx, dloss):
+        (dQ,) = ctx.saved_tensors
+        return dQ * dloss.view(-1, 1, 1), None, None, None
+
+
 def render(theta, W, engine: RenderEngine):
     """Q[B, D, D] = Rasterize(theta, W) (Algorithm 2), differentiable in theta."""
     return _Render.apply(theta, W, engine)
@@ -123,9 +150,15 @@ def loss(X, Y, D, reduction=0):
     return _Loss.apply(X, Y, L.config(D, reduction=reduction))
 
 
+def ctf_loss(Q, ctf, Y, engine: RenderEngine):
+    """Per-image L = ||CTF(Q) - Y||^2 (App. A.2 Eq. 14, Sec. 3.3.5), differentiable in Q: the
+    value of loss(apply_ctf(Q, ctf), Y) in one call that does not form X."""
+    return _CTFLoss.apply(Q, ctf, Y, engine)
+
+
 def main(argv=None):
     """Training steps through the autograd path at scale, the lists recomputed in the
-    backward: one step = render -> CTF -> loss -> backward -> Adam over the whole batch.
+    backward: one step = render -> CTF + loss -> backward -> Adam over the whole batch.
     Prints one JSON line (images/s, ms per step, peak device memory)."""
     import argparse
     import json
@@ -160,7 +193,7 @@ def main(argv=None):
 
     def step():
         theta.grad = None
-        Ls = loss(apply_ctf(render(theta, W, eng), C, eng), Y, a.D).sum()
+        Ls = ctf_loss(render(theta, W, eng), C, Y, eng).sum()
         Ls.backward()
         with torch.no_grad():
             L.gs_step_counted(theta.data, theta.grad, m, v, t_dev, lr=1e-3)

@@ -57,6 +57,32 @@ def test_autograd_gradient_matches_oracle_with_recomputed_lists():
     eng.close()
 
 
+@pytest.mark.parametrize("D", [48, 256])
+def test_fused_ctf_loss_matches_composed_and_oracle(D):
+    """ctf_loss(render(theta)) gives the loss and gradient of loss(apply_ctf(render(theta))),
+    and the oracle's (D = 256: the row-transform + column-kernel path)."""
+    th, Ws, ctf, Y = _inputs(seed=44, D=D, N=300, B=5)
+    B = Ws.shape[0]
+    ref = O.forward_backward(th, Ws, D, Y, ctf)
+    eng = AG.RenderEngine(D, th.shape[0], particles_per_chunk=2, tile=8, chunk=64)
+    W = torch.from_numpy(Ws.reshape(B, 9)).cuda()
+    C = torch.from_numpy(ctf).cuda()
+    Yd = torch.from_numpy(Y).cuda()
+    t1 = torch.from_numpy(th).cuda().requires_grad_(True)
+    L1 = AG.ctf_loss(AG.render(t1, W, eng), C, Yd, eng)
+    L1.sum().backward()
+    t2 = torch.from_numpy(th).cuda().requires_grad_(True)
+    L2 = _loss_fn(eng, W, C, Yd, D)(t2)
+    L2.backward()
+    assert np.allclose(L1.detach().cpu().numpy(), ref["L"], rtol=1e-5)
+    assert abs(float(L1.sum().detach()) - float(L2.detach())) < 2e-6 * float(L2.detach())
+    g1, g2 = t1.grad.cpu().numpy(), t2.grad.cpu().numpy()
+    for name, sl in GROUPS:
+        assert np.linalg.norm(g1[:, sl] - g2[:, sl]) < 1e-5 * np.linalg.norm(g2[:, sl]), name
+        assert np.linalg.norm(g1[:, sl] - ref["dtheta"][:, sl]) < 1e-3 * np.linalg.norm(ref["dtheta"][:, sl]), name
+    eng.close()
+
+
 def test_directional_difference_of_cuda_forward():
     """<grad L, v> against (L(theta + e v) - L(theta - e v)) / 2e computed by the CUDA forward
     itself.  The support boxes are integer decisions, so v is restricted to the Gaussians
