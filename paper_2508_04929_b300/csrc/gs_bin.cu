@@ -9,7 +9,7 @@
 //
 //   k_bin_count   (chunk, b): per-chunk tile histogram (chunk = kBinChunk Gaussians)
 //   k_bin_scan    (b):        per tile, exclusive scan over chunks; exclusive scan over tiles
-//   k_bin_base    (1 CTA):    exclusive scan over particles (64-bit), total instance count
+//   k_bin_base    (1 warp):   exclusive scan over particles (64-bit), total instance count
 //   k_bin_scatter (chunk, b): stable ranks inside the chunk (8 warps in order, 32 lanes in
 //                             order), scatter of the Gaussian indices, tile ranges
 //
@@ -202,32 +202,37 @@ __global__ void __launch_bounds__(1024) k_bin_scan(uint32_t* __restrict__ hist, 
   }
   __syncthreads();
   uint32_t total = block_exclusive_scan(sh, Tn);
-  for (int t = threadIdx.x; t < Tn; t += blockDim.x) {
-    const uint32_t st = sh[t];
-    tstart[(size_t)b * Tn + t] = st;
-    for (int c0 = 0; c0 < C; c0 += kBatch) {
-      uint32_t v[kBatch];
-#pragma unroll
-      for (int j = 0; j < kBatch; ++j) v[j] = (c0 + j < C) ? H[(size_t)(c0 + j) * Tn + t] : 0u;
-#pragma unroll
-      for (int j = 0; j < kBatch; ++j)
-        if (c0 + j < C) H[(size_t)(c0 + j) * Tn + t] = v[j] + st;
-    }
-  }
+  // the chunk offsets stay relative to the tile's start; k_bin_scatter adds tstart
+  for (int t = threadIdx.x; t < Tn; t += blockDim.x) tstart[(size_t)b * Tn + t] = sh[t];
   if (threadIdx.x == 0) itotal[b] = total;
 }
 
+// Exclusive scan over the particles' instance counts (64-bit) by one warp: each lane sums a
+// contiguous run of particles, the lanes' sums are scanned by shuffles, and each lane writes
+// its run's bases.
 __global__ void k_bin_base(const uint32_t* __restrict__ itotal, int B, unsigned long long* __restrict__ ibase,
                            uint32_t* __restrict__ n_pairs, unsigned long long cap, int* __restrict__ status) {
-  if (threadIdx.x != 0) return;
-  unsigned long long run = 0;
-  for (int b = 0; b < B; ++b) {
+  const int lane = threadIdx.x;
+  const int per = (B + 31) / 32, b0 = min(B, lane * per), b1 = min(B, b0 + per);
+  unsigned long long mine = 0;
+  for (int b = b0; b < b1; ++b) mine += itotal[b];
+  unsigned long long incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  unsigned long long run = incl - mine;
+  for (int b = b0; b < b1; ++b) {
     ibase[b] = run;
     run += itotal[b];
   }
-  ibase[B] = run;
-  *n_pairs = run > 0xffffffffull ? 0xffffffffu : (uint32_t)run;
-  if (run > cap) atomicOr(status, GS_STATUS_OVERFLOW);
+  const unsigned long long total = __shfl_sync(0xffffffffu, incl, 31);
+  if (lane == 0) {
+    ibase[B] = total;
+    *n_pairs = total > 0xffffffffull ? 0xffffffffu : (uint32_t)total;
+    if (total > cap) atomicOr(status, GS_STATUS_OVERFLOW);
+  }
 }
 
 __global__ void k_bin_scatter(const int2* __restrict__ boxes, int N, int sh, int ntx, int Tn, int C,
@@ -266,10 +271,11 @@ __global__ void k_bin_scatter(const int2* __restrict__ boxes, int N, int sh, int
       for (int tx = r.tx0; tx <= r.tx1; ++tx) atomicAdd(&mycur[ty * ntx + tx], 1u);
   }
   __syncthreads();
-  // 2. exclusive scan over warps, offset by this chunk's start within the image
+  // 2. exclusive scan over warps, offset by this chunk's start within the image (the tile's
+  // start plus the chunk's offset inside the tile)
   const uint32_t* Hc = hist + ((size_t)b * C + c) * Tn;
   for (int t = threadIdx.x; t < Tn; t += blockDim.x) {
-    uint32_t run = Hc[t];
+    uint32_t run = Hc[t] + tstart[(size_t)b * Tn + t];
     for (int w = 0; w < kBinWarps; ++w) {
       uint32_t v = cur[w * Tn + t];
       cur[w * Tn + t] = run;
