@@ -44,9 +44,9 @@ CTF_SNR = 0.05
 # each render kernel, from the capture summarised in profiles/render_kernels_d256_n100k_b64.md
 # (B = 64; the kernels read each pair's index and record once, so traffic scales with the pair
 # count).  Valid only for the gs_render.cu whose SHA-256 is recorded: otherwise null.
-RENDER_TRAFFIC = {"sha256": "32d116bf69feb054c6fc50db367bf0c5b6b49a2a9dbc62d625825af0ffbe4b10",
-                  "bytes_per_pair": {"fwd": (306.626560e6 + 16.540160e6) / 25319264,
-                                     "bwd": (320.808448e6 + 3.612928e6) / 25319264}}
+RENDER_TRAFFIC = {"sha256": "92ed4920a696104654ce04bab43f557b4e7f907cabb25baa0b586194e508a0bc",
+                  "bytes_per_pair": {"fwd": (306.633472e6 + 16.611584e6) / 25319264,
+                                     "bwd": (320.488192e6 + 3.123456e6) / 25319264}}
 
 
 # libgs kernels launched by one graph-captured training step (cuFFT's and torch's gradient
