@@ -1,8 +1,8 @@
 """Parity at the full sizes of the workloads, in the launch configurations that are timed: the
 bench's graph-captured step (D = 256, N = 100k, B = 128, tile 8, the fused CTF-loss path), the
-batched fused step at D = 128, N = 20k, B = 64 (autotuned), and the autograd step at scale
+batched fused step at D = 128, N = 20k, B = 64 (autotuned), the autograd step at scale
 (D = 256, N = 200k Gaussians on random-walk chains, B = 256, lists recomputed per 64-particle
-chunk).  The FP64 oracle computes sampled images' losses and dL/dQ and one image's gradient,
+chunk) and the mixed batch of four volumes (D = 96-256, N = 10k-100k, 128 particles each).  The FP64 oracle computes sampled images' losses and dL/dQ and one image's gradient,
 taken from inside the full batch launch; the tile counts are compared in full (bit-exact)."""
 import numpy as np
 import pytest
@@ -115,3 +115,42 @@ def test_autograd_step_at_scale():
             for name, sl in GROUPS:
                 assert rel_l2(g[:, sl], ref[:, sl]) < 1e-3, name
     eng.close()
+
+
+def test_mixed_batch_full_size():
+    """Four volumes in one graph: N = 10k/30k/60k/100k at D = 96/128/192/256, 128 particles each,
+    launch shapes autotuned per volume; one sampled image's loss and dL/dQ per volume and one
+    image's gradient for the smallest volume."""
+    dev = torch.device(DEV)
+    specs = [(96, 10_000), (128, 30_000), (192, 60_000), (256, 100_000)]
+    made = []
+    for k, (D, N) in enumerate(specs):
+        rng = synth.rng_for(20 + k)
+        th = synth.random_gaussians(N, D, rng)
+        Ws = synth.random_poses(128, rng)
+        ctf = synth.random_ctf(128, rng)
+        Y = synth.smooth_field(128, D, rng, scale=1.0)
+        p = Problem(D=D, theta=torch.from_numpy(th).to(dev), W=torch.from_numpy(Ws.reshape(128, 9)).to(dev),
+                    ctf=torch.from_numpy(ctf).to(dev), Y=torch.from_numpy(Y).to(dev))
+        made.append((p, th, Ws, ctf, Y))
+    gs = GraphStep([m[0] for m in made], adam=False, autotune_chunks=(64, 128))
+    losses = [x.cpu().numpy() for x in gs.replay()]
+    torch.cuda.synchronize()
+    assert gs.check() == 0
+    for (p, th, Ws, ctf, Y), lo, (D, N) in zip(made, losses, specs):
+        b = 31
+        L_ref, dQ_ref = oracle_image(th, Ws[b], ctf[b], Y[b], D)
+        assert abs(lo[b] - L_ref) <= 1e-5 * L_ref, (D, lo[b], L_ref)
+        assert rel_l2(p.sp.dQ[b].cpu().numpy(), dQ_ref) < 1e-5, D
+    p, th, Ws, ctf, Y = made[0]
+    D = specs[0][0]
+    g_img = np.zeros((128, D, D), np.float32)
+    g_img[3] = p.sp.dQ[3].cpu().numpy()
+    p.sp.project(p.theta, p.W)
+    dth = torch.zeros_like(p.theta)
+    p.sp.backward(p.theta, p.W, torch.from_numpy(g_img).to(dev), dth)
+    ref = O.backward(th, Ws[3:4], D, g_img[3:4].astype(np.float64))
+    g = dth.cpu().numpy()
+    for name, sl in GROUPS:
+        assert rel_l2(g[:, sl], ref[:, sl]) < 1e-3, name
+    gs.close()
