@@ -5,7 +5,7 @@
 // amplitude, quaternion normalization, R(q) and M = R diag(s).  k_project forms, per
 // (particle, Gaussian), mu_dot = W mu, Sigma_tilde = (W M)_{2x3} (W M)_{2x3}^T, the k-sigma
 // support box and the record consumed by the rasterizer; a thread serves one Gaussian for
-// four particles.
+// sixteen particles, so that the Gaussian's row of the activated table is read once for them.
 //
 // The support box is an integer decision.  It is computed with explicitly rounded FP32
 // intrinsics (no FMA contraction) in a fixed order, so that any FP32 implementation of the
@@ -87,7 +87,7 @@ __global__ void k_activate(const float* __restrict__ theta, int N, float* __rest
   if (bad) atomicOr(status, GS_STATUS_NONFINITE);
 }
 
-constexpr int kProjParticles = 4;  // particles per thread: one load of the Gaussian's row serves them all
+constexpr int kProjParticles = 16;  // particles per thread: one load of the Gaussian's row serves them all
 
 // One 32-byte store: the record fills its sector in a single request (proj 32-byte aligned).
 __device__ __forceinline__ void st_record32(gs_record* dst, const gs_record& r) {
