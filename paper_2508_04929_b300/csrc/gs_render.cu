@@ -5,9 +5,10 @@
 // order) is dealt to the lanes: entry j goes to lane j mod 32.  A lane evaluates its
 // Gaussian on all 64 pixels of the block (an "item"), so the per-Gaussian set-up is paid
 // once per block and no per-pixel test is needed beyond the box's row and column masks.
-//   - Tiles of 8 pixels: each warp of a CTA owns one tile; its lanes read their records
-//     straight from global memory (the tile's list is the block's list), one record and
-//     two pair indices ahead; the forward also prefetches the record after next into L1.
+//   - Tiles of 8 pixels: each warp of a CTA owns one tile of a 2 x 2 quad (Gaussians shared by
+//     neighbouring tiles then meet in the same L1); its lanes read their records straight
+//     from global memory (the tile's list is the block's list), one record and two pair
+//     indices ahead; the forward also prefetches the record after next into L1.
 //   - Tiles of 16 or 32 pixels: a CTA of four warps covers a 16 x 16 region (the tile, or
 //     a quadrant of a 32-pixel tile), stages the tile's records through shared memory in
 //     chunks, and each warp compacts, by ballots, the records whose box touches its block.
@@ -75,6 +76,14 @@ __device__ __forceinline__ float lg2_approx(float x) {
   float y;
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
+}
+
+
+// Tile of warp w in CTA q: CTAs tile the image in 2 x 2 quads of tiles, (-1 past the image).
+__device__ __forceinline__ int quad_tile(int q, int w, int ntx) {
+  const int nqx = (ntx + 1) >> 1;
+  const int tx = 2 * (q % nqx) + (w & 1), ty = 2 * (q / nqx) + (w >> 1);
+  return (tx < ntx && ty < ntx) ? ty * ntx + tx : -1;
 }
 
 struct Rec {
@@ -338,8 +347,8 @@ __global__ void __launch_bounds__(kTileWarps * 32, kFwd8MinBlocks) k_render_fwd8
     const gs_record* __restrict__ proj, int N, const uint32_t* __restrict__ pair_gauss,
     const uint32_t* __restrict__ ranges, int D, int ntx, float* __restrict__ Q) {
   const int lane = threadIdx.x & 31, b = blockIdx.y;
-  const int tile = blockIdx.x * kTileWarps + (threadIdx.x >> 5);
-  if (tile >= ntx * ntx) return;  // warp-uniform
+  const int tile = quad_tile(blockIdx.x, threadIdx.x >> 5, ntx);
+  if (tile < 0) return;  // warp-uniform
   const int X = (tile % ntx) * kB, Y = (tile / ntx) * kB;
   const size_t rr = ((size_t)b * ntx * ntx + tile) * 2;
   const uint32_t start = ranges[rr], end = ranges[rr + 1];
@@ -389,8 +398,8 @@ __global__ void __launch_bounds__(kTileWarps * 32) k_render_bwd8(const gs_record
                                                                  float* __restrict__ dpose) {
   __shared__ __align__(16) u64 g2all[kTileWarps][kB][4];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, b = blockIdx.y;
-  const int tile = blockIdx.x * kTileWarps + warp;
-  if (tile >= ntx * ntx) return;  // warp-uniform
+  const int tile = quad_tile(blockIdx.x, warp, ntx);
+  if (tile < 0) return;  // warp-uniform
   const int X = (tile % ntx) * kB, Y = (tile / ntx) * kB;
   const size_t rr = ((size_t)b * ntx * ntx + tile) * 2;
   const uint32_t start = ranges[rr], end = ranges[rr + 1];
@@ -670,7 +679,7 @@ cudaError_t launch_render_fwd(const gs_config& cfg, const gs_record* proj, int N
   if (B <= 0) return cudaSuccess;
   const int ntx = (cfg.D + cfg.tile - 1) / cfg.tile;
   if (cfg.tile == 8) {
-    const dim3 grid((ntx * ntx + kTileWarps - 1) / kTileWarps, B);
+    const dim3 grid(((ntx + 1) / 2) * ((ntx + 1) / 2), B);
     k_render_fwd8<<<grid, kTileWarps * 32, 0, s>>>(proj, N, pair_gauss, ranges, cfg.D, ntx, Q);
     return cudaGetLastError();
   }
@@ -692,7 +701,7 @@ cudaError_t launch_render_bwd(const gs_config& cfg, const gs_record* proj, int N
   const int ntx = (cfg.D + cfg.tile - 1) / cfg.tile;
   const float h = 2.f * cfg.E / (float)cfg.D;
   if (cfg.tile == 8) {
-    const dim3 grid((ntx * ntx + kTileWarps - 1) / kTileWarps, B);
+    const dim3 grid(((ntx + 1) / 2) * ((ntx + 1) / 2), B);
     if (dpose)
       k_render_bwd8<true><<<grid, kTileWarps * 32, 0, s>>>(proj, N, pair_gauss, ranges, cfg.D, ntx, dLdQ, W, h, wacc,
                                                             gauss, dpose);
