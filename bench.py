@@ -44,9 +44,9 @@ CTF_SNR = 0.05
 # each render kernel, from the capture summarised in profiles/render_kernels_d256_n100k_b64.md
 # (B = 64; the kernels read each pair's index and record once, so traffic scales with the pair
 # count).  Valid only for the gs_render.cu whose SHA-256 is recorded: otherwise null.
-RENDER_TRAFFIC = {"sha256": "92ed4920a696104654ce04bab43f557b4e7f907cabb25baa0b586194e508a0bc",
-                  "bytes_per_pair": {"fwd": (306.633472e6 + 16.611584e6) / 25319264,
-                                     "bwd": (320.488192e6 + 3.123456e6) / 25319264}}
+RENDER_TRAFFIC = {"sha256": "83e6a01f13d28f6924fae7245e34518128f32d7a45f11a7b8e2682cdc8f48f5c",
+                  "bytes_per_pair": {"fwd": (306.648064e6 + 16.967168e6) / 25319264,
+                                     "bwd": (320.490240e6 + 3.575552e6) / 25319264}}
 
 
 # libgs kernels launched by one graph-captured training step (cuFFT's and torch's gradient
