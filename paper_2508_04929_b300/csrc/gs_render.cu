@@ -8,7 +8,7 @@
 //   - Tiles of 8 pixels: each warp of a CTA owns one tile of a 2 x 2 quad (Gaussians shared by
 //     neighbouring tiles then meet in the same L1); its lanes read their records straight
 //     from global memory (the tile's list is the block's list), one record and two pair
-//     indices ahead; the forward also prefetches the record after next into L1.
+//     indices ahead; the forward also prefetches the record two items ahead into L1.
 //   - Tiles of 16 or 32 pixels: a CTA of four warps covers a 16 x 16 region (the tile, or
 //     a quadrant of a 32-pixel tile), stages the tile's records through shared memory in
 //     chunks, and each warp compacts, by ballots, the records whose box touches its block.
@@ -359,11 +359,11 @@ __global__ void __launch_bounds__(kTileWarps * 32, kFwd8MinBlocks) k_render_fwd8
   for (int u = 0; u < kB; ++u)
 #pragma unroll
     for (int rp = 0; rp < 4; ++rp) acc[u][rp] = pk(0.f, 0.f);
-  // record of the current item in (na, nb); Gaussian indices of the next two in g1, g2; the
-  // record after next is prefetched into L1 so that its load one item ahead hits there
+  // record of the current item in (na, nb); Gaussian indices of the next three in g1, g2, g3;
+  // the record two items ahead is prefetched into L1 so that its load one item ahead hits there
   uint32_t i = start + lane;
   float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na;
-  uint32_t g1 = 0, g2 = 0;
+  uint32_t g1 = 0, g2 = 0, g3 = 0;
   if (i < end) {
     const uint32_t g0 = min(pair_gauss[i], gmax);
     na = __ldg(pr + 2 * (size_t)g0);
@@ -371,15 +371,18 @@ __global__ void __launch_bounds__(kTileWarps * 32, kFwd8MinBlocks) k_render_fwd8
   }
   if (i + 32 < end) g1 = min(pair_gauss[i + 32], gmax);
   if (i + 64 < end) g2 = min(pair_gauss[i + 64], gmax);
+  if (i + 64 < end) asm volatile("prefetch.global.L1 [%0];" ::"l"(pr + 2 * (size_t)g2));
+  if (i + 96 < end) g3 = min(pair_gauss[i + 96], gmax);
   while (i < end) {
     const Rec r = rec_from(na, nb);
     i += 32;
     if (i < end) {
       na = __ldg(pr + 2 * (size_t)g1);
       nb = __ldg(pr + 2 * (size_t)g1 + 1);
-      if (i + 32 < end) asm volatile("prefetch.global.L1 [%0];" ::"l"(pr + 2 * (size_t)g2));
+      if (i + 64 < end) asm volatile("prefetch.global.L1 [%0];" ::"l"(pr + 2 * (size_t)g3));
       g1 = g2;
-      if (i + 64 < end) g2 = min(pair_gauss[i + 64], gmax);
+      g2 = g3;
+      if (i + 96 < end) g3 = min(pair_gauss[i + 96], gmax);
     }
     Item it = make_item(r, X, Y);
     fwd_item(it, acc);
