@@ -44,9 +44,9 @@ CTF_SNR = 0.05
 # each render kernel, from the capture summarised in profiles/render_kernels_d256_n100k_b64.md
 # (B = 64; the kernels read each pair's index and record once, so traffic scales with the pair
 # count).  Valid only for the gs_render.cu whose SHA-256 is recorded: otherwise null.
-RENDER_TRAFFIC = {"sha256": "83e6a01f13d28f6924fae7245e34518128f32d7a45f11a7b8e2682cdc8f48f5c",
-                  "bytes_per_pair": {"fwd": (306.648064e6 + 16.967168e6) / 25319264,
-                                     "bwd": (320.490240e6 + 3.575552e6) / 25319264}}
+RENDER_TRAFFIC = {"sha256": "ba1ff0a67305ce3af7c224d32f6d3c4449b11d4cd079e294746a21858487fefa",
+                  "bytes_per_pair": {"fwd": (306.685696e6 + 16.518144e6) / 25319264,
+                                     "bwd": (320.492288e6 + 3.127040e6) / 25319264}}
 
 
 # libgs kernels launched by one graph-captured training step (cuFFT's and torch's gradient
