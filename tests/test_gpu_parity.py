@@ -195,6 +195,31 @@ def test_fused_ctf_loss_grad_matches_oracle(D, reduction):
     sp.close()
 
 
+def test_scale_activation_is_the_rounded_fp64_softplus():
+    """The scales of the activated table are fp32(softplus in FP64) bit for bit (the support
+    box depends on them): inside the range of the float-float evaluation, beyond it, and at
+    its ends.  The table is the first array of the workspace after the 256-byte status block,
+    24 floats per Gaussian with the scales at 12..14."""
+    rng = np.random.default_rng(9)
+    raw = np.concatenate([rng.uniform(-60, 17, 200_000), rng.uniform(-90, 40, 50_000), rng.normal(-4.9, 1.0, 50_000),
+                          [-60.0, -59.999, 17.0, 17.0001, 0.0, -0.0, 1e-30, -1e-30, 30.0]]).astype(np.float32)
+    n = (len(raw) + 2) // 3
+    flat = np.zeros(3 * n, np.float32)
+    flat[:len(raw)] = raw
+    th = np.zeros((n, 11), np.float32)
+    th[:, 6] = 1.0
+    th[:, 3:6] = flat.reshape(n, 3)
+    sp = Splatter(64, n, 1, tile=8, with_ctf=False)
+    sp.project(torch.from_numpy(th).to(DEV), torch.eye(3, device=DEV).reshape(1, 9))
+    torch.cuda.synchronize()
+    table = sp.ws[256:256 + n * 96].view(torch.float32).view(n, 24).cpu().numpy()
+    got = np.ascontiguousarray(table[:, 12:15]).reshape(-1)
+    x = flat.astype(np.float64)
+    ref = (np.maximum(x, 0.0) + np.log1p(np.exp(-np.abs(x)))).astype(np.float32)
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32)), int(np.sum(got != ref))
+    sp.close()
+
+
 def test_adam_step_matches_oracle():
     rng = synth.rng_for(5)
     th = rng.standard_normal(11 * 500).astype(np.float32)
