@@ -235,22 +235,26 @@ __global__ void k_bin_base(const uint32_t* __restrict__ itotal, int B, unsigned 
   }
 }
 
-__global__ void k_bin_scatter(const int2* __restrict__ boxes, int N, int sh, int ntx, int Tn, int C,
+__global__ void k_bin_scatter(const int2* __restrict__ boxes, int N, int sh, int ntx, int Tn, int sp, int C,
                               const uint32_t* __restrict__ hist, const uint32_t* __restrict__ tstart,
                               const uint32_t* __restrict__ ttotal,
                               const unsigned long long* __restrict__ ibase, uint32_t* __restrict__ pair_gauss,
                               unsigned long long cap, uint32_t* __restrict__ ranges) {
-  extern __shared__ uint32_t cur[];  // [kBinWarps][Tn], [kBinWarps][32] window owners, [65] k / w multipliers
+  // shared: [kBinWarps][ntx rows of sp] cursors, [kBinWarps][32] window owners, [65] k / w multipliers.
+  // The cursor rows are sp = 3 (mod 32) words apart, so the tiles of a small box, which a window
+  // touches together, fall in distinct banks (tx + 3 ty differs for boxes up to 3 tiles wide)
+  extern __shared__ uint32_t cur[];
+  const int Tp = ntx * sp;
   const int c = blockIdx.x, b = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned long long base = ibase[b];
-  for (int i = threadIdx.x; i < kBinWarps * Tn; i += blockDim.x) cur[i] = 0;
+  for (int i = threadIdx.x; i < kBinWarps * Tp; i += blockDim.x) cur[i] = 0;
   __syncthreads();
   const int per_warp = kBinChunk / kBinWarps;
   const int g0 = c * kBinChunk + warp * per_warp;
   const int g1 = min(N, g0 + per_warp);
-  uint32_t* mycur = cur + warp * Tn;
-  int* slot = reinterpret_cast<int*>(cur + kBinWarps * Tn) + warp * 32;
+  uint32_t* mycur = cur + warp * Tp;
+  int* slot = reinterpret_cast<int*>(cur + kBinWarps * Tp) + warp * 32;
   const int2* bx = boxes + (size_t)b * N;
   // floor(2^20 / w) + 1 for box widths w = 1..64: (k * m) >> 20 = k / w exactly for k < 4096
   unsigned* divmul = reinterpret_cast<unsigned*>(slot + (kBinWarps - warp) * 32);
@@ -268,7 +272,7 @@ __global__ void k_bin_scatter(const int2* __restrict__ boxes, int N, int sh, int
     TileRect r;
     if (!unpack_rect(bxs[j], sh, r)) continue;
     for (int ty = r.ty0; ty <= r.ty1; ++ty)
-      for (int tx = r.tx0; tx <= r.tx1; ++tx) atomicAdd(&mycur[ty * ntx + tx], 1u);
+      for (int tx = r.tx0; tx <= r.tx1; ++tx) atomicAdd(&mycur[ty * sp + tx], 1u);
   }
   __syncthreads();
   // 2. exclusive scan over warps, offset by this chunk's start within the image (the tile's
@@ -276,9 +280,10 @@ __global__ void k_bin_scatter(const int2* __restrict__ boxes, int N, int sh, int
   const uint32_t* Hc = hist + ((size_t)b * C + c) * Tn;
   for (int t = threadIdx.x; t < Tn; t += blockDim.x) {
     uint32_t run = Hc[t] + tstart[(size_t)b * Tn + t];
+    const int ty = t / ntx, tp = ty * sp + (t - ty * ntx);
     for (int w = 0; w < kBinWarps; ++w) {
-      uint32_t v = cur[w * Tn + t];
-      cur[w * Tn + t] = run;
+      uint32_t v = cur[w * Tp + tp];
+      cur[w * Tp + tp] = run;
       run += v;
     }
   }
@@ -344,7 +349,7 @@ __global__ void k_bin_scatter(const int2* __restrict__ boxes, int N, int sh, int
         if (ty >= 32) rm = r1;
       }
       const unsigned both = cm & rm;  // lanes of this round whose box covers (tx, ty)
-      const int t = ty * ntx + tx;
+      const int t = ty * sp + tx;
       if (act) {
         const unsigned long long pos = base + mycur[t] + __popc(both & ((1u << owner) - 1u));
         if (pos < cap) pair_gauss[pos] = (uint32_t)(gr + owner);
@@ -400,13 +405,14 @@ cudaError_t launch_bin(const gs_config& cfg, const WsLayout& L, const gs_record*
   }
   k_bin_scan<<<B, 1024, sm_count, s>>>(hist, Tn, C, tstart, ttotal, itotal);
   k_bin_base<<<1, 32, 0, s>>>(itotal, B, ibase, n_pairs, (unsigned long long)cap, status);
-  size_t sm_scatter = sizeof(uint32_t) * (kBinWarps * (Tn + 32) + 65);
+  const int sp = ntx + ((35 - ntx) & 31);  // cursor row stride, 3 (mod 32)
+  size_t sm_scatter = sizeof(uint32_t) * (kBinWarps * (ntx * sp + 32) + 65);
   {
     static int cache[64] = {0};
     e = ensure_smem((const void*)k_bin_scatter, sm_scatter, cache);
     if (e != cudaSuccess) return e;
   }
-  k_bin_scatter<<<g2, 32 * kBinWarps, sm_scatter, s>>>(boxes, N, sh, ntx, Tn, C, hist, tstart, ttotal, ibase,
+  k_bin_scatter<<<g2, 32 * kBinWarps, sm_scatter, s>>>(boxes, N, sh, ntx, Tn, sp, C, hist, tstart, ttotal, ibase,
                                                       pair_gauss, (unsigned long long)cap, ranges);
   return cudaGetLastError();
 }
