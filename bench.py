@@ -51,8 +51,13 @@ RENDER_TRAFFIC = {"sha256": "ba1ff0a67305ce3af7c224d32f6d3c4449b11d4cd079e294746
 
 # libgs kernels launched by one graph-captured training step (cuFFT's and torch's gradient
 # zeroing are library kernels and not counted)
-STEP_KERNELS = ("k_activate", "k_project", "k_bin_count", "k_bin_scan", "k_bin_base", "k_bin_scatter",
-                "k_render_fwd8", "k_ctf_loss", "k_render_bwd8", "k_bwd_finalize", "k_adam", "k_count_step")
+def step_kernels(D, tile):
+    """The library's kernels that one graph-captured training step launches, once each (the
+    cuFFT row transforms of the D = 256 path and torch's zeroing of the gradient are not ours)."""
+    r = "8" if tile == 8 else "16"  # tiles 16 and 32 share the region kernels
+    return ("k_activate", "k_project", "k_bin_count", "k_bin_scan", "k_bin_tiles", "k_bin_base", "k_bin_scatter",
+            "k_render_fwd" + r, "k_ctf_cols" if D == 256 else "k_ctf_loss", "k_render_bwd" + r, "k_bwd_finalize",
+            "k_adam", "k_count_step")
 
 
 def parse():
@@ -527,7 +532,7 @@ def main():
             "speedup_vs_plain": (value / world / plain) if plain else None,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "pipelining": "next step's host->device copy overlaps the current step; every step's losses are copied back and read by the host one step later"},
-            "gpu_launches": len(STEP_KERNELS) * args.steps,
+            "gpu_launches": len(step_kernels(args.D, tile)) * args.steps,
             "roofline": {"bound": "alu", "kernel": f"k_render_{dom}", "achieved": achieved / 1e9,
                          "peak": peak_exp / 1e9, "unit": "Gex2/s", "frac": achieved / peak_exp,
                          "traffic": render_traffic(dom, n_pairs), "peak_source": "measured ex2 rate x 148 SMs x max SM clock"},

@@ -8,7 +8,8 @@
 // histogram gives the tile ranges directly.
 //
 //   k_bin_count   (chunk, b): per-chunk tile histogram (chunk = kBinChunk Gaussians)
-//   k_bin_scan    (b):        per tile, exclusive scan over chunks; exclusive scan over tiles
+//   k_bin_scan    (tiles, b): per tile, exclusive scan over chunks
+//   k_bin_tiles   (b):        exclusive scan over tiles
 //   k_bin_base    (1 warp):   exclusive scan over particles (64-bit), total instance count
 //   k_bin_scatter (chunk, b): stable ranks inside the chunk (8 warps in order, 32 lanes in
 //                             order), scatter of the Gaussian indices, tile ranges
@@ -179,29 +180,43 @@ __device__ uint32_t block_exclusive_scan(uint32_t* v, int n) {
   return total;
 }
 
-__global__ void __launch_bounds__(1024) k_bin_scan(uint32_t* __restrict__ hist, int Tn, int C, uint32_t* __restrict__ tstart,
-                           uint32_t* __restrict__ ttotal, uint32_t* __restrict__ itotal) {
+// Per tile, the exclusive scan of its counts over the chunks, in place (each chunk's offset
+// inside the tile's run), and the tile's total; 256 tiles of one particle image per CTA.  The
+// loads of the next 8 chunks are issued before the stores of the current 8.
+__global__ void __launch_bounds__(256) k_bin_scan(uint32_t* __restrict__ hist, int Tn, int C,
+                                                  uint32_t* __restrict__ ttotal) {
+  const int b = blockIdx.y, t = blockIdx.x * 256 + (int)threadIdx.x;
+  if (t >= Tn) return;
+  uint32_t* H = hist + (size_t)b * C * Tn + t;
+  constexpr int kBatch = 8;
+  uint32_t nxt[kBatch];
+#pragma unroll
+  for (int j = 0; j < kBatch; ++j) nxt[j] = j < C ? H[(size_t)j * Tn] : 0u;
+  uint32_t run = 0;
+  for (int c0 = 0; c0 < C; c0 += kBatch) {
+    uint32_t v[kBatch];
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) v[j] = nxt[j];
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) nxt[j] = c0 + kBatch + j < C ? H[(size_t)(c0 + kBatch + j) * Tn] : 0u;
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+      if (c0 + j < C) H[(size_t)(c0 + j) * Tn] = run;
+      run += v[j];
+    }
+  }
+  ttotal[(size_t)b * Tn + t] = run;
+}
+
+// Per particle image, the exclusive scan of the tile totals (each tile's start inside the
+// image's instances) and the image's total.
+__global__ void __launch_bounds__(1024) k_bin_tiles(const uint32_t* __restrict__ ttotal, int Tn,
+                                                    uint32_t* __restrict__ tstart, uint32_t* __restrict__ itotal) {
   extern __shared__ uint32_t sh[];  // Tn
   const int b = blockIdx.x;
-  uint32_t* H = hist + (size_t)b * C * Tn;
-  constexpr int kBatch = 8;  // independent loads in flight per thread
-  for (int t = threadIdx.x; t < Tn; t += blockDim.x) {
-    uint32_t run = 0;
-    for (int c0 = 0; c0 < C; c0 += kBatch) {
-      uint32_t v[kBatch];
-#pragma unroll
-      for (int j = 0; j < kBatch; ++j) v[j] = (c0 + j < C) ? H[(size_t)(c0 + j) * Tn + t] : 0u;
-#pragma unroll
-      for (int j = 0; j < kBatch; ++j) {
-        if (c0 + j < C) H[(size_t)(c0 + j) * Tn + t] = run;
-        run += v[j];
-      }
-    }
-    sh[t] = run;
-    ttotal[(size_t)b * Tn + t] = run;
-  }
+  for (int t = threadIdx.x; t < Tn; t += blockDim.x) sh[t] = ttotal[(size_t)b * Tn + t];
   __syncthreads();
-  uint32_t total = block_exclusive_scan(sh, Tn);
+  const uint32_t total = block_exclusive_scan(sh, Tn);
   // the chunk offsets stay relative to the tile's start; k_bin_scatter adds tstart
   for (int t = threadIdx.x; t < Tn; t += blockDim.x) tstart[(size_t)b * Tn + t] = sh[t];
   if (threadIdx.x == 0) itotal[b] = total;
@@ -400,10 +415,11 @@ cudaError_t launch_bin(const gs_config& cfg, const WsLayout& L, const gs_record*
   k_bin_count<<<g2, 256, sm_count, s>>>(boxes, N, sh, ntx, Tn, C, hist);
   {
     static int cache[64] = {0};
-    e = ensure_smem((const void*)k_bin_scan, sm_count, cache);
+    e = ensure_smem((const void*)k_bin_tiles, sm_count, cache);
     if (e != cudaSuccess) return e;
   }
-  k_bin_scan<<<B, 1024, sm_count, s>>>(hist, Tn, C, tstart, ttotal, itotal);
+  k_bin_scan<<<dim3((Tn + 255) / 256, B), 256, 0, s>>>(hist, Tn, C, ttotal);
+  k_bin_tiles<<<B, 1024, sm_count, s>>>(ttotal, Tn, tstart, itotal);
   k_bin_base<<<1, 32, 0, s>>>(itotal, B, ibase, n_pairs, (unsigned long long)cap, status);
   const int sp = ntx + ((35 - ntx) & 31);  // cursor row stride, 3 (mod 32)
   size_t sm_scatter = sizeof(uint32_t) * (kBinWarps * (ntx * sp + 32) + 65);
