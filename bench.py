@@ -44,9 +44,9 @@ CTF_SNR = 0.05
 # each render kernel, from the capture summarised in profiles/render_kernels_d256_n100k_b64.md
 # (B = 64; the kernels read each pair's index and record once, so traffic scales with the pair
 # count).  Valid only for the gs_render.cu whose SHA-256 is recorded: otherwise null.
-RENDER_TRAFFIC = {"sha256": "ba1ff0a67305ce3af7c224d32f6d3c4449b11d4cd079e294746a21858487fefa",
-                  "bytes_per_pair": {"fwd": (306.685696e6 + 16.518144e6) / 25319264,
-                                     "bwd": (320.492288e6 + 3.127040e6) / 25319264}}
+RENDER_TRAFFIC = {"sha256": "0b4202ef93b2706a3ad155e37863ac654e03b6f39e07132977cfc2f61c9e90fb",
+                  "bytes_per_pair": {"fwd": (306.640128e6 + 16.543744e6) / 25319262,
+                                     "bwd": (320.496640e6 + 3.529472e6) / 25319262}}
 
 
 # libgs kernels launched by one graph-captured training step (cuFFT's and torch's gradient

@@ -329,28 +329,40 @@ template <bool kCounted, bool kVec>
 __global__ void k_adam(float* __restrict__ th, const float* __restrict__ g, float* __restrict__ m,
                        float* __restrict__ v, int n, const int* __restrict__ t_dev, float lr, float b1, float b2,
                        float eps, float c1, float c2) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  const int n4 = kVec ? n / 4 : 0;
+  float4* th4 = reinterpret_cast<float4*>(th);
+  float4* m4 = reinterpret_cast<float4*>(m);
+  float4* v4 = reinterpret_cast<float4*>(v);
+  const float4* g4 = reinterpret_cast<const float4*>(g);
+  // the thread's first four values are loaded before the bias corrections are known
+  float4 T = make_float4(0.f, 0.f, 0.f, 0.f), M = T, V = T, G = T;
+  if (kVec && tid < n4) {
+    T = th4[tid];
+    M = m4[tid];
+    V = v4[tid];
+    G = g4[tid];
+  }
   if (kCounted) {
+    // the two FP64 bias corrections on two warps at once (FP64 pow is slow on this part)
     __shared__ float cc[2];
-    if (threadIdx.x == 0) {
+    if ((threadIdx.x & 31) == 0 && threadIdx.x < 64) {
+      const int k = threadIdx.x >> 5;
       const double t = (double)(*t_dev + 1);
-      cc[0] = (float)(1.0 / (1.0 - pow((double)b1, t)));
-      cc[1] = (float)(1.0 / (1.0 - pow((double)b2, t)));
+      cc[k] = (float)(1.0 / (1.0 - pow((double)(k == 0 ? b1 : b2), t)));
     }
     __syncthreads();
     c1 = cc[0];
     c2 = cc[1];
   }
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-  int done = 0;
   if (kVec) {
-    const int n4 = n / 4;
-    float4* th4 = reinterpret_cast<float4*>(th);
-    float4* m4 = reinterpret_cast<float4*>(m);
-    float4* v4 = reinterpret_cast<float4*>(v);
-    const float4* g4 = reinterpret_cast<const float4*>(g);
     for (int i = tid; i < n4; i += stride) {
-      float4 T = th4[i], M = m4[i], V = v4[i];
-      const float4 G = g4[i];
+      if (i != tid) {
+        T = th4[i];
+        M = m4[i];
+        V = v4[i];
+        G = g4[i];
+      }
       adam_one(T.x, G.x, M.x, V.x, lr, b1, b2, eps, c1, c2);
       adam_one(T.y, G.y, M.y, V.y, lr, b1, b2, eps, c1, c2);
       adam_one(T.z, G.z, M.z, V.z, lr, b1, b2, eps, c1, c2);
@@ -359,14 +371,13 @@ __global__ void k_adam(float* __restrict__ th, const float* __restrict__ g, floa
       m4[i] = M;
       v4[i] = V;
     }
-    done = 4 * n4;
   }
-  for (int i = done + tid; i < n; i += stride) {
-    float T = th[i], M = m[i], V = v[i];
-    adam_one(T, g[i], M, V, lr, b1, b2, eps, c1, c2);
-    th[i] = T;
-    m[i] = M;
-    v[i] = V;
+  for (int i = 4 * n4 + tid; i < n; i += stride) {
+    float Ts = th[i], Ms = m[i], Vs = v[i];
+    adam_one(Ts, g[i], Ms, Vs, lr, b1, b2, eps, c1, c2);
+    th[i] = Ts;
+    m[i] = Ms;
+    v[i] = Vs;
   }
 }
 

@@ -595,15 +595,11 @@ __global__ void __launch_bounds__(kRegionWarps * 32) k_render_bwd16(const gs_rec
   if (kPose) pose_flush(pacc, dpose + (size_t)b * 12);
 }
 
-// Per Gaussian: dL/dA = sum S0 / A and the chain from (grad_mu, grad_Sigma) to theta.
-// Re-zeroes the accumulator it consumed.
-__global__ void k_bwd_finalize(const float* __restrict__ theta, const float* __restrict__ gauss, int N,
-                               float* __restrict__ wacc, float* __restrict__ dtheta) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= N) return;
-  const float* G = gauss + (size_t)g * kGaussStride;
+// dL/dTheta of one Gaussian from its accumulated sums: dL/dA = sum S0 / A, and the chain from
+// (grad_mu, grad_Sigma) to theta through the activations.  Adds to out[11] and re-zeroes the
+// accumulator it consumed.
+__device__ __forceinline__ void finalize_one(const float* G, const float* th, float* acc, float* out) {
   if (G[kBad] != 0.f) return;
-  float* acc = wacc + (size_t)g * 12;
   const float4 a0 = reinterpret_cast<const float4*>(acc)[0];
   const float4 a1 = reinterpret_cast<const float4*>(acc)[1];
   const float4 a2 = reinterpret_cast<const float4*>(acc)[2];
@@ -638,7 +634,6 @@ __global__ void k_bwd_finalize(const float* __restrict__ theta, const float* __r
       dR[3 * k + m] = dM[3 * k + m] * s[m];
     }
   }
-  const float* th = theta + (size_t)g * 11;
   const float qw = th[6], qx = th[7], qy = th[8], qz = th[9];
   const float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
   const float w = qw / qn, x = qx / qn, y = qy / qn, zq = qz / qn;
@@ -652,7 +647,6 @@ __global__ void k_bwd_finalize(const float* __restrict__ theta, const float* __r
   const float dz = dR[0] * (-4.f * zq) + dR[1] * (-2.f * w) + dR[2] * (2.f * x) + dR[3] * (2.f * w) +
                    dR[4] * (-4.f * zq) + dR[5] * (2.f * y) + dR[6] * (2.f * x) + dR[7] * (2.f * y);
   const float dot = w * dw + x * dx + y * dy + zq * dz;
-  float* out = dtheta + (size_t)g * 11;
   out[0] += gmu[0];
   out[1] += gmu[1];
   out[2] += gmu[2];
@@ -663,6 +657,38 @@ __global__ void k_bwd_finalize(const float* __restrict__ theta, const float* __r
   out[8] += (dy - y * dot) / qn;
   out[9] += (dz - zq * dot) / qn;
   out[10] += gA / (1.f + expf(-th[10]));
+}
+
+constexpr int kFinG = 128;     // Gaussians per finalize CTA, one per thread
+constexpr int kFinGRow = kGaussStride + 1;  // padded table row in shared memory (no bank conflicts)
+
+// The per-Gaussian rows (activated table, Theta, dL/dTheta) are staged through shared memory
+// with coalesced loads; each thread then works on its own Gaussian's row.
+__global__ void __launch_bounds__(kFinG) k_bwd_finalize(const float* __restrict__ theta,
+                                                       const float* __restrict__ gauss, int N,
+                                                       float* __restrict__ wacc, float* __restrict__ dtheta) {
+  __shared__ float sG[kFinG * kFinGRow];
+  __shared__ float sT[kFinG * 11];
+  __shared__ float sD[kFinG * 11];
+  const int g0 = blockIdx.x * kFinG;
+  const int n = min(kFinG, N - g0);
+  const float* gsrc = gauss + (size_t)g0 * kGaussStride;
+  for (int i = threadIdx.x; i < n * kGaussStride; i += kFinG) {
+    const int r = i / kGaussStride;
+    sG[r * kFinGRow + (i - r * kGaussStride)] = __ldg(gsrc + i);
+  }
+  const float* tsrc = theta + (size_t)g0 * 11;
+  float* dsrc = dtheta + (size_t)g0 * 11;
+  for (int i = threadIdx.x; i < n * 11; i += kFinG) {
+    sT[i] = __ldg(tsrc + i);
+    sD[i] = dsrc[i];
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < n) finalize_one(sG + threadIdx.x * kFinGRow, sT + threadIdx.x * 11,
+                                         wacc + (size_t)(g0 + threadIdx.x) * kGradStride,
+                                         sD + threadIdx.x * 11);
+  __syncthreads();
+  for (int i = threadIdx.x; i < n * 11; i += kFinG) dsrc[i] = sD[i];
 }
 
 }  // namespace
@@ -732,7 +758,7 @@ cudaError_t launch_render_bwd(const gs_config& cfg, const gs_record* proj, int N
 cudaError_t launch_bwd_finalize(const float* theta, const float* gauss, int N, float* wacc, float* dtheta,
                                 cudaStream_t s) {
   if (N <= 0) return cudaSuccess;
-  k_bwd_finalize<<<(N + 255) / 256, 256, 0, s>>>(theta, gauss, N, wacc, dtheta);
+  k_bwd_finalize<<<(N + kFinG - 1) / kFinG, kFinG, 0, s>>>(theta, gauss, N, wacc, dtheta);
   return cudaGetLastError();
 }
 

@@ -283,6 +283,50 @@ def test_large_gaussian_covering_many_tiles():
         assert rel_l2(out["dtheta"][:, sl], ref["dtheta"][:, sl]) < 1e-3, name
 
 
+@pytest.mark.parametrize("D,tile,full", [(384, 8, True), (512, 8, False), (1024, 16, False)])
+def test_wide_tile_grids(D, tile, full):
+    """More than 32 tiles per side (up to the 64 the binning allows), where the scatter takes
+    the second word of its transposed lane masks.  A few large Gaussians near the centre make
+    boxes cross tile 32.  Pair lists and ranges bit-exact; at D = 384 also the images and
+    gradients."""
+    rng = synth.rng_for(40 + D)
+    th = synth.random_gaussians(300, D, rng)
+    th[:6, 0:3] = rng.uniform(-0.05, 0.05, size=(6, 3))
+    th[:6, 3:6] = synth.inv_softplus(np.array([40.0, 25.0, 60.0]) / D)
+    Ws = synth.random_poses(2, rng)
+    ctf = synth.random_ctf(2, rng)
+    pg, ranges = O.tile_pairs(th, Ws, D, tile)
+    tx1 = []
+    for b in range(2):
+        x0, x1, y0, y1 = O.support_fp32(th, Ws[b], D)[:4]
+        tx1.append((np.asarray(x1) // tile >= 32) & (np.asarray(x0) // tile < 32))
+    assert np.concatenate(tx1).any()  # some boxes straddle tile column 32
+    if full:
+        Y = synth.add_noise(np.stack([O.apply_ctf(O.render_one(th, Ws[b], D), O.ctf_image(
+            D, *[float(v) for v in ctf[b, 0:4]], apix=float(ctf[b, 4]))) for b in range(2)]), 0.1, rng)
+        ref = O.forward_backward(th, Ws, D, Y, ctf)
+        out = cuda_step(th, Ws, ctf, Y, D, tile=tile)
+        for b in range(2):
+            assert rel_l2(out["Q"][b], ref["Q"][b]) < 1e-5
+        for name, sl in GROUPS:
+            assert rel_l2(out["dtheta"][:, sl], ref["dtheta"][:, sl]) < 1e-3, name
+        pairs, rng_out, n = out["pairs"], out["ranges"], out["n_pairs"]
+    else:
+        sp = Splatter(D, th.shape[0], 2, tile=tile, with_ctf=False)
+        t, W = to_dev(th, Ws.reshape(2, 9))
+        sp.project(t, W)
+        sp.bin_sort(grow=True)
+        torch.cuda.synchronize()
+        n = int(sp.n_pairs.item()) & 0xFFFFFFFF
+        pairs = sp.pairs.cpu().numpy().view(np.uint32)
+        rng_out = sp.ranges.cpu().numpy().view(np.uint32)
+        assert sp.status() == 0
+        sp.close()
+    assert n == len(pg)
+    assert np.array_equal(pairs[: len(pg)], pg)
+    assert np.array_equal(rng_out.reshape(ranges.shape), ranges)
+
+
 def test_pair_overflow_is_reported_and_recovered(c1):
     th, Ws, ctf, Y, ref = c1
     sp = Splatter(64, th.shape[0], Ws.shape[0], tile=16, pair_capacity=100)
