@@ -323,8 +323,8 @@ __device__ __forceinline__ void adam_one(float& th, float g, float& m, float& v,
 
 // Adam over n floats, four per thread and iteration when all buffers are 16-byte aligned
 // (kVec), with a grid of two CTAs per SM.  kCounted: the step counter is on the device
-// (t_dev = steps already taken) so that a captured graph can be replayed; the bias
-// corrections are then formed in FP64 by one thread per CTA.
+// (t_dev = steps already taken) so that a captured graph can be replayed; each CTA then forms
+// the two bias corrections in FP64, one per warp of its first two.
 template <bool kCounted, bool kVec>
 __global__ void k_adam(float* __restrict__ th, const float* __restrict__ g, float* __restrict__ m,
                        float* __restrict__ v, int n, const int* __restrict__ t_dev, float lr, float b1, float b2,
