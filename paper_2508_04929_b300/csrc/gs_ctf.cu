@@ -33,11 +33,8 @@ __device__ __forceinline__ void ctf_constants(const float* __restrict__ ctf, int
   cst[4] = (float)w;
 }
 
-// H_hat at half-spectrum element idx = l (D / 2 + 1) + m (row l, column m) of a D x D image.
-__device__ __forceinline__ float ctf_value(int idx, int D, int W2, const float cst[5]) {
-  const int l = idx / W2, m = idx - l * W2;
-  const int fy = l < (D + 1) / 2 ? l : l - D;
-  const float n = (float)(fy * fy + m * m);  // exact (< 2^24)
+// H_hat at squared frequency index n = fy^2 + m^2 (exact in FP32, < 2^24).
+__device__ __forceinline__ float ctf_value_n(float n, const float cst[5]) {
   const float p = cst[0] * n;
   const float perr = fmaf(cst[0], n, -p);        // exact remainder of alpha_hi * n
   const float pred = p - 2.f * rintf(0.5f * p);  // exact: p mod 2 in [-1, 1]
@@ -47,6 +44,13 @@ __device__ __forceinline__ float ctf_value(int idx, int D, int W2, const float c
   float sp, cp;
   sincospif(tt, &sp, &cp);
   return -(cst[3] * sp + cst[4] * cp);
+}
+
+// H_hat at half-spectrum element idx = l (D / 2 + 1) + m (row l, column m) of a D x D image.
+__device__ __forceinline__ float ctf_value(int idx, int D, int W2, const float cst[5]) {
+  const int l = idx / W2, m = idx - l * W2;
+  const int fy = l < (D + 1) / 2 ? l : l - D;
+  return ctf_value_n((float)(fy * fy + m * m), cst);
 }
 
 __global__ void k_ctf_mul(float2* __restrict__ spec, const float* __restrict__ ctf, int D) {
@@ -168,6 +172,7 @@ __global__ void __cluster_dims__(kLossCtas, 1, 1) k_ctf_loss(float2* __restrict_
 // adds the CTAs' sums in index order.
 // ---------------------------------------------------------------------------------------
 constexpr int kColD = 256, kColW2 = kColD / 2 + 1, kColNC = 16;
+static_assert(kColNC == 16, "k_ctf_cols indexes its CTF table with e >> 4 and e & 15");
 static_assert(kColCtas == (kColW2 + kColNC - 1) / kColNC, "CTAs per image of k_ctf_cols");
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -247,6 +252,7 @@ __global__ void __launch_bounds__(256) k_ctf_cols(float2* __restrict__ qr, const
   float2* ay = csm + kColD * kColNC;     // [256][16]
   float2* tw = csm + 2 * kColD * kColNC; // [256]
   __shared__ float cst[5];
+  __shared__ float Hs[(kColD / 2 + 1) * kColNC];  // H at rows ky = 0..128 (row D - ky has the same |k|)
   __shared__ float red[8];
   __shared__ bool last;
   const int b = blockIdx.y, c0 = blockIdx.x * kColNC;
@@ -267,9 +273,15 @@ __global__ void __launch_bounds__(256) k_ctf_cols(float2* __restrict__ qr, const
     ay[y * kColNC + j] = col ? yr[gi] : make_float2(0.f, 0.f);
   }
   __syncthreads();
+  {
+    const float c[5] = {cst[0], cst[1], cst[2], cst[3], cst[4]};
+    for (int e = threadIdx.x; e < (kColD / 2 + 1) * kColNC; e += blockDim.x) {
+      const int ky = e >> 4, kx = c0 + (e & 15);
+      Hs[e] = ctf_value_n((float)(ky * ky + kx * kx), c);
+    }
+  }
   fft256_cols<false>(aq, tw);
   fft256_cols<false>(ay, tw);
-  const float c[5] = {cst[0], cst[1], cst[2], cst[3], cst[4]};
   const float inv_d2 = 1.f / ((float)kColD * (float)kColD);
   const float gscale = 2.f * scale * inv_d2;
   const int kx = c0 + j;
@@ -278,7 +290,7 @@ __global__ void __launch_bounds__(256) k_ctf_cols(float2* __restrict__ qr, const
 #pragma unroll 4
   for (int r = 0; r < 16; ++r) {
     const int ky = sub + 16 * r;
-    const float H = ctf_value(ky * kColW2 + kx, kColD, kColW2, c);
+    const float H = Hs[(ky <= kColD / 2 ? ky : kColD - ky) * kColNC + j];
     const float2 qv = aq[ky * kColNC + j], yv = ay[ky * kColNC + j];
     const float zx = fmaf(H, qv.x, -yv.x), zy = fmaf(H, qv.y, -yv.y);
     if (col) acc = fmaf(wgt, fmaf(zx, zx, zy * zy), acc);
