@@ -10,7 +10,10 @@ their own poses, CTF parameters and observed images -- into a single CUDA graph:
 Problems of a mixed batch (different D and N) run on their own streams inside the graph,
 so small volumes overlap large ones; one ``replay()`` launches the whole batch.  Inputs
 change between steps by copying into the static buffers (``load``); the Adam step counter
-lives on the device so replays need no host values.  The pair buffers are sized by an
+lives on the device so replays need no host values.  The step can also be replayed as two
+graphs, ``replay_front()`` (projection, binning, render: it reads the poses only) and
+``replay_back()`` (CTF, loss, backward, Adam: the observed images), so that a step's images
+may still be arriving while its front half runs.  The pair buffers are sized by an
 eager pass with a margin; ``check()`` reads the status words (a host sync) and re-sizes and
 re-records if a step ever needed more pairs.  The tile size and chunk depth of every
 problem come from the autotuner unless given.
@@ -74,6 +77,7 @@ class GraphStep:
             p.t = torch.zeros(1, dtype=torch.int32, device=self.dev)
         self.streams = [torch.cuda.Stream(device=self.dev) for _ in self.problems]
         self.graph = None
+        self.graph_front = self.graph_back = None  # recorded on first use
         self._size_pairs()
         self._record()
 
@@ -88,26 +92,34 @@ class GraphStep:
             L.gs_clear_status(p.sp.ws)
         torch.cuda.synchronize(self.dev)
 
-    def _body(self, p):
+    def _front(self, p):
         sp = p.sp
         p.dtheta.zero_()
         sp.project(p.theta, p.W)
         sp.bin_sort(grow=False)
         sp.render()
+
+    def _back(self, p):
+        sp = p.sp
         sp.ctf_loss_grad(sp.Q, p.ctf, p.Y)
         sp.backward(p.theta, p.W, sp.dQ, p.dtheta)
         if self.adam:
             L.gs_step_counted(p.theta, p.dtheta, p.m, p.v, p.t, lr=p.lr)
 
-    def _run_all(self):
+    def _body(self, p):
+        self._front(p)
+        self._back(p)
+
+    def _run_all(self, part=None):
+        body = part or self._body
         main = torch.cuda.current_stream(self.dev)
         if len(self.problems) == 1:
-            self._body(self.problems[0])
+            body(self.problems[0])
             return
         for p, s in zip(self.problems, self.streams):
             s.wait_stream(main)
             with torch.cuda.stream(s):
-                self._body(p)
+                body(p)
         for s in self.streams:
             main.wait_stream(s)
 
@@ -124,10 +136,23 @@ class GraphStep:
         torch.cuda.synchronize(self.dev)
         for p, (th, m, v, t) in zip(self.problems, saved):
             p.theta.copy_(th); p.m.copy_(m); p.v.copy_(v); p.t.copy_(t)
-        self.graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(self.graph, capture_error_mode="thread_local"):
-            self._run_all()
+        self.graph = self._capture(None)
+        self.graph_front = self.graph_back = None
+
+    def _capture(self, part):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, capture_error_mode="thread_local"):
+            self._run_all(part)
         torch.cuda.synchronize(self.dev)
+        return g
+
+    def record_split(self):
+        """Record the two halves of the step (done on first use otherwise).  The whole step
+        has been warmed and recorded already, so its halves need no warm-up."""
+        if not self.use_graph:
+            return
+        self.graph_front = self._capture(self._front)
+        self.graph_back = self._capture(self._back)
 
     # -- use -------------------------------------------------------------------------------
     def load(self, i, W=None, ctf=None, Y=None):
@@ -143,6 +168,26 @@ class GraphStep:
             self.graph.replay()
         else:
             self._run_all()
+        return [p.sp.loss[: p.B] for p in self.problems]
+
+    def replay_front(self):
+        """The first half of a step (projection, binning, render); reads theta and W."""
+        if not self.use_graph:
+            self._run_all(self._front)
+            return
+        if self.graph_front is None:
+            self.record_split()
+        self.graph_front.replay()
+
+    def replay_back(self):
+        """The second half (CTF, loss, backward, Adam); reads ctf and Y.  Returns the
+        per-image loss tensors (device)."""
+        if not self.use_graph:
+            self._run_all(self._back)
+        else:
+            if self.graph_back is None:
+                self.record_split()
+            self.graph_back.replay()
         return [p.sp.loss[: p.B] for p in self.problems]
 
     def check(self):
@@ -167,7 +212,9 @@ class HostFeeder:
     """Double-buffered feeding of one problem of a GraphStep from pinned host memory: the
     next step's (W, ctf, Y) are copied host -> device on a side stream while the current step
     runs, and ``load()`` moves them into the graph's static buffers (a device-to-device copy on
-    the current stream) just before the replay."""
+    the current stream) just before the replay.  ``load_front()`` and ``load_back()`` split
+    that for ``replay_front()`` / ``replay_back()``: the poses and CTF parameters are copied
+    first, so that a step's front half can start while its images are still arriving."""
 
     def __init__(self, gs: GraphStep, i=0):
         p = gs.problems[i]
@@ -175,6 +222,7 @@ class HostFeeder:
         self.copy_stream = torch.cuda.Stream(device=p.theta.device)
         self.bufs = [tuple(torch.empty_like(x) for x in (p.W, p.ctf, p.Y)) for _ in range(2)]
         self.ready = [torch.cuda.Event() for _ in range(2)]
+        self.ready_small = [torch.cuda.Event() for _ in range(2)]  # W and ctf
         self.free = [torch.cuda.Event() for _ in range(2)]
         self.filled = 0
         self.used = 0
@@ -184,8 +232,10 @@ class HostFeeder:
         j = self.filled % 2
         self.copy_stream.wait_event(self.free[j])  # its previous contents have been loaded
         with torch.cuda.stream(self.copy_stream):
-            for dst, src in zip(self.bufs[j], (W, ctf, Y)):
+            for dst, src in zip(self.bufs[j][:2], (W, ctf)):
                 dst.copy_(src, non_blocking=True)
+            self.ready_small[j].record(self.copy_stream)
+            self.bufs[j][2].copy_(Y, non_blocking=True)
         self.ready[j].record(self.copy_stream)
         self.filled += 1
 
@@ -196,5 +246,22 @@ class HostFeeder:
         cur.wait_event(self.ready[j])
         W, ctf, Y = self.bufs[j]
         self.gs.load(self.i, W=W, ctf=ctf, Y=Y)
+        self.free[j].record(cur)
+        self.used += 1
+
+    def load_front(self):
+        """The oldest prefetched poses and CTF parameters become the current ones."""
+        j = self.used % 2
+        cur = torch.cuda.current_stream()
+        cur.wait_event(self.ready_small[j])
+        W, ctf, _ = self.bufs[j]
+        self.gs.load(self.i, W=W, ctf=ctf)
+
+    def load_back(self):
+        """... and their images; completes the load that ``load_front()`` began."""
+        j = self.used % 2
+        cur = torch.cuda.current_stream()
+        cur.wait_event(self.ready[j])
+        self.gs.load(self.i, Y=self.bufs[j][2])
         self.free[j].record(cur)
         self.used += 1

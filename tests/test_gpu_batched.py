@@ -17,7 +17,7 @@ from paper_2508_04929_b300 import build  # noqa: E402
 
 build.build()
 from paper_2508_04929_b300 import _lib as L  # noqa: E402
-from paper_2508_04929_b300.batched import GraphStep, Problem  # noqa: E402
+from paper_2508_04929_b300.batched import GraphStep, HostFeeder, Problem  # noqa: E402
 from paper_2508_04929_b300.splat import Splatter  # noqa: E402
 
 GROUPS = (slice(0, 3), slice(3, 6), slice(6, 10), slice(10, 11))
@@ -104,6 +104,66 @@ def test_replay_with_new_inputs_and_counted_adam():
     d = (p.theta - t).abs().cpu().numpy()
     assert np.mean(d > 1e-5) < 0.01 and d.max() <= 4.1e-3  # Adam may flip the sign of ~0 gradients
     sp.close()
+    gs.close()
+
+
+def test_split_replay_equals_whole_step():
+    """replay_front() + replay_back() is the step that replay() runs: the same first loss bit for
+    bit, and then the same losses and Theta up to the order of the backward's float atomics."""
+    p, _ = _problem(63, 40, 400, 4)
+    th0 = p.theta.clone()
+    gs = GraphStep([p], adam=True)
+    la = [gs.replay()[0].cpu().numpy() for _ in range(3)]
+    tha = p.theta.clone()
+    p.theta.copy_(th0)
+    p.m.zero_()
+    p.v.zero_()
+    p.t.zero_()
+    gs.record_split()
+    lb = []
+    for _ in range(3):
+        gs.replay_front()
+        lb.append(gs.replay_back()[0].cpu().numpy())
+    torch.cuda.synchronize()
+    assert np.array_equal(la[0], lb[0])
+    for x, y in zip(la[1:], lb[1:]):
+        assert np.allclose(x, y, rtol=1e-5)
+    d = (p.theta - tha).abs().cpu().numpy()
+    assert np.mean(d > 1e-5) < 0.01 and d.max() <= 4.1e-3  # Adam may flip the sign of ~0 gradients
+    assert int(p.t.item()) == 3
+    gs.close()
+
+
+def test_host_feeder_halves_match_whole_loads():
+    """Feeding a step in two parts (poses and CTF before the front half, images before the
+    back half) gives the losses of feeding it whole, step after step."""
+    p, _ = _problem(64, 40, 400, 4)
+    gs = GraphStep([p], adam=False)
+    rng = synth.rng_for(65)
+    batches = [(torch.from_numpy(synth.random_poses(4, rng).reshape(4, 9)).pin_memory(),
+                torch.from_numpy(synth.random_ctf(4, rng)).pin_memory(),
+                torch.from_numpy(synth.smooth_field(4, 40, rng, scale=100.0)).pin_memory()) for _ in range(3)]
+    whole, halves = [], []
+    fa = HostFeeder(gs)
+    fa.prefetch(*batches[0])
+    for i in range(3):
+        fa.load()
+        if i + 1 < 3:
+            fa.prefetch(*batches[i + 1])
+        whole.append(gs.replay()[0].clone())
+    fb = HostFeeder(gs)
+    fb.prefetch(*batches[0])
+    for i in range(3):
+        fb.load_front()
+        if i + 1 < 3:
+            fb.prefetch(*batches[i + 1])
+        gs.replay_front()
+        fb.load_back()
+        halves.append(gs.replay_back()[0].clone())
+    torch.cuda.synchronize()
+    for x, y in zip(whole, halves):
+        assert torch.equal(x, y)
+    assert not torch.equal(whole[0], whole[1])  # the steps did take new inputs
     gs.close()
 
 
