@@ -283,16 +283,21 @@ def test_large_gaussian_covering_many_tiles():
         assert rel_l2(out["dtheta"][:, sl], ref["dtheta"][:, sl]) < 1e-3, name
 
 
-@pytest.mark.parametrize("D,tile,full", [(384, 8, True), (512, 8, False), (1024, 16, False)])
-def test_wide_tile_grids(D, tile, full):
+@pytest.mark.parametrize("D,tile,mode", [(384, 8, "full"), (512, 8, "pairs"), (1024, 16, "pairs"),
+                                         (2048, 32, "image")])
+def test_wide_tile_grids(D, tile, mode):
     """More than 32 tiles per side (up to the 64 the binning allows), where the scatter takes
     the second word of its transposed lane masks.  A few large Gaussians near the centre make
-    boxes cross tile 32.  Pair lists and ranges bit-exact; at D = 384 also the images and
-    gradients."""
+    boxes cross tile 32; at D = 2048 (the largest image) they cover most of the 64 x 64 tiles.
+    Pair lists and ranges bit-exact; at D = 384 also the images and gradients, at D = 2048 the
+    rendered images.  FP32 pixel coordinates carry an absolute error that grows with D (the
+    unit in the last place of D / 2), and a splat's value moves with its centre, so the image
+    bar is 1e-5 scaled by D / 256 (the largest box of the paper's workloads)."""
+    full = mode == "full"
     rng = synth.rng_for(40 + D)
     th = synth.random_gaussians(300, D, rng)
     th[:6, 0:3] = rng.uniform(-0.05, 0.05, size=(6, 3))
-    th[:6, 3:6] = synth.inv_softplus(np.array([40.0, 25.0, 60.0]) / D)
+    th[:6, 3:6] = synth.inv_softplus(np.array([40.0, 25.0, 60.0]) * max(1.0, D / 1024.0) / D)
     Ws = synth.random_poses(2, rng)
     ctf = synth.random_ctf(2, rng)
     pg, ranges = O.tile_pairs(th, Ws, D, tile)
@@ -316,6 +321,11 @@ def test_wide_tile_grids(D, tile, full):
         t, W = to_dev(th, Ws.reshape(2, 9))
         sp.project(t, W)
         sp.bin_sort(grow=True)
+        if mode == "image":
+            sp.render()
+            Q = sp.Q.cpu().numpy()
+            for b in range(2):
+                assert rel_l2(Q[b], O.render_one(th, Ws[b], D)) < 1e-5 * max(1.0, D / 256)
         torch.cuda.synchronize()
         n = int(sp.n_pairs.item()) & 0xFFFFFFFF
         pairs = sp.pairs.cpu().numpy().view(np.uint32)
@@ -325,6 +335,44 @@ def test_wide_tile_grids(D, tile, full):
     assert n == len(pg)
     assert np.array_equal(pairs[: len(pg)], pg)
     assert np.array_equal(rng_out.reshape(ranges.shape), ranges)
+
+
+EPS32 = 2.0 ** -24
+
+
+@pytest.mark.parametrize("ratio", [10, 40])
+def test_needles_and_pancakes(ratio):
+    """Strong anisotropy: needles (one axis of 8 px, two of 8 / ratio px) and pancakes (one thin
+    axis) in random orientations.  Boxes bit-exact.  The image's FP32 error grows with the
+    condition number kappa = ratio^2 of the 2 x 2 covariance (the exponent's expanded quadratic
+    form cancels), and the thin scale's gradient carries one more factor of the ratio: the bars
+    are max(1e-5, 2 eps kappa) for images and max(1e-3, 2 eps ratio^3) for gradients, eps = 2^-24.
+    The paper's workloads have ratios of at most 6."""
+    rng = synth.rng_for(77)
+    D, N, B = 64, 60, 4
+    th = synth.random_gaussians(N, D, rng)
+    thin = 8.0 / ratio
+    sc = np.where(np.arange(N)[:, None] % 2 == 0, np.array([thin, 8.0, thin]), np.array([8.0, 6.0, thin]))
+    th[:, 3:6] = synth.inv_softplus(sc / D)
+    Ws = synth.random_poses(B, rng)
+    ctf = synth.random_ctf(B, rng)
+    Y = synth.add_noise(np.stack([O.apply_ctf(O.render_one(synth.random_gaussians(N, D, rng), Ws[b], D),
+                                              O.ctf_image(D, *[float(v) for v in ctf[b, 0:4]],
+                                                          apix=float(ctf[b, 4]))) for b in range(B)]), 0.1, rng)
+    ref = O.forward_backward(th, Ws, D, Y, ctf)
+    out = cuda_step(th, Ws, ctf, Y, D, tile=8)
+    for b in range(B):
+        x0, x1, y0, y1 = O.support_fp32(th, Ws[b], D)[:4]
+        empty = (np.asarray(x0) > np.asarray(x1)) | (np.asarray(y0) > np.asarray(y1))
+        box = out["box"][b]
+        assert np.array_equal(empty, box[:, 0] > box[:, 1])
+        ok = ~empty
+        assert np.array_equal(box[ok], np.stack([x0, x1, y0, y1], 1)[ok])
+        tol = max(1e-5, 2 * EPS32 * ratio ** 2)
+        assert rel_l2(out["Q"][b], ref["Q"][b]) < tol
+        assert rel_l2(out["X"][b], ref["X"][b]) < tol
+    for name, sl in GROUPS:
+        assert rel_l2(out["dtheta"][:, sl], ref["dtheta"][:, sl]) < max(1e-3, 2 * EPS32 * ratio ** 3), name
 
 
 def test_pair_overflow_is_reported_and_recovered(c1):
