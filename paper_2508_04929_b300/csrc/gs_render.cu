@@ -202,12 +202,15 @@ __device__ __forceinline__ void bwd_item(Item& it, const u64 (*g2)[4], const Rec
     const bool on = (it.cm >> u) & 1u;
     const float uc = (float)u - 3.5f;
     const u64 U = pk(uc, uc), U2 = pk(uc * uc, uc * uc);
+    const ulonglong2 ga = reinterpret_cast<const ulonglong2*>(g2[u])[0];
+    const ulonglong2 gb = reinterpret_cast<const ulonglong2*>(g2[u])[1];
+    const u64 gg[4] = {ga.x, ga.y, gb.x, gb.y};
 #pragma unroll
     for (int rp = 0; rp < 4; ++rp) {
       float e0, e1;
       upk(it.E[rp], e0, e1);
       const u64 V = pk(ex2_approx(e0), ex2_approx(e1));
-      const u64 t = on ? mul2(g2[u][rp], V) : 0ull;  // +0.0 in both halves
+      const u64 t = on ? mul2(gg[rp], V) : 0ull;  // +0.0 in both halves
       A[rp] = add2(A[rp], t);
       Bm[rp] = fma2(U, t, Bm[rp]);
       C[rp] = fma2(U2, t, C[rp]);
