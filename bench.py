@@ -44,9 +44,9 @@ CTF_SNR = 0.05
 # each render kernel, from the capture summarised in profiles/render_kernels_d256_n100k_b64.md
 # (B = 64; the kernels read each pair's index and record once, so traffic scales with the pair
 # count).  Valid only for the gs_render.cu whose SHA-256 is recorded: otherwise null.
-RENDER_TRAFFIC = {"sha256": "0b4202ef93b2706a3ad155e37863ac654e03b6f39e07132977cfc2f61c9e90fb",
-                  "bytes_per_pair": {"fwd": (306.640128e6 + 16.543744e6) / 25319262,
-                                     "bwd": (320.496640e6 + 3.529472e6) / 25319262}}
+RENDER_TRAFFIC = {"sha256": "6a4c04e970708d894f77b790d82b11d0ff960c93249a835ab7b26e497e6fad34",
+                  "bytes_per_pair": {"fwd": (306.627840e6 + 16.727552e6) / 25319264,
+                                     "bwd": (320.502784e6 + 3.731968e6) / 25319264}}
 
 
 # libgs kernels launched by one graph-captured training step (cuFFT's and torch's gradient
