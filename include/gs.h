@@ -85,8 +85,8 @@ typedef struct gs_fft {
   int D;
   int B;
   size_t work_bytes; /* cuFFT work area needed (placed inside the gs workspace) */
-  int r2c_rows;      /* cufftHandle: 1-D R2C of the B * D rows (D = 256 only, else 0) */
-  int c2r_rows;      /* cufftHandle: 1-D C2R of the B * D rows (D = 256 only, else 0) */
+  int r2c_rows;      /* reserved, 0 (the D = 256 row transforms are the library's own kernels) */
+  int c2r_rows;      /* reserved, 0 */
 } gs_fft;
 
 /* ---------------------------------------------------------------------------------------
@@ -193,11 +193,13 @@ int gs_loss(const gs_config* cfg, const float* X, const float* Y, int B, float* 
  * |Z|^2 / D^2 (s = 1 for reduction 0, 1 / D^2 for reduction 1), and
  * dLdQ = C2R(2 s H_hat Z) / D^2 is the adjoint CTF of dL/dX = 2 s (X - Y): the values of
  * gs_apply_ctf + gs_loss + gs_apply_ctf up to FP32 rounding, with three FFTs instead of
- * four.  For D = 256 the 2-D transforms are split: cuFFT transforms the rows, and one kernel
- * runs the column FFTs of Q and Y, the pointwise step and the inverse column FFT together
- * (four passes over the spectra instead of seven).  Q, Y, dLdQ [B * D * D]; ctf as for gs_apply_ctf; dLdQ may alias Q.  Uses cuFFT
- * (fft created for this D and B) and two half spectra plus the work area at the tail of
- * ws (gs_workspace_size includes them). */
+ * four.  For D = 256 the library's own kernels do all of it: one launch transforms the rows
+ * of Q and Y (one complex FFT of Q + iY per row, split by Hermitian symmetry), one kernel
+ * runs the column FFTs of both, the pointwise step and the inverse column FFT, and one
+ * launch transforms the rows back (two real rows per complex FFT); other sizes use cuFFT's
+ * 2-D transforms (fft created for this D and B).  Q, Y, dLdQ [B * D * D]; ctf as for
+ * gs_apply_ctf; dLdQ may alias Q.  Two half spectra and the work area sit at the tail of ws
+ * (gs_workspace_size includes them). */
 int gs_ctf_loss_grad(const gs_config* cfg, const float* Q, const float* Y, const float* ctf, int B,
                      float* loss, float* dLdQ, const gs_fft* fft, void* ws, size_t ws_bytes,
                      gs_stream_t stream);

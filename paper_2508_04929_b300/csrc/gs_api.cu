@@ -80,28 +80,6 @@ int gs_fft_create(int D, int B, gs_fft* fft) {
   fft->r2c = (int)a;
   fft->c2r = (int)c;
   fft->work_bytes = wa > wc ? wa : wc;
-  if (D == 256) {  // row transforms for the column kernel of gs_ctf_loss_grad
-    cufftHandle ar, cr;
-    if (cufftCreate(&ar) != CUFFT_SUCCESS) { gs_fft_destroy(fft); return GS_ECUDA; }
-    if (cufftCreate(&cr) != CUFFT_SUCCESS) { cufftDestroy(ar); gs_fft_destroy(fft); return GS_ECUDA; }
-    cufftSetAutoAllocation(ar, 0);
-    cufftSetAutoAllocation(cr, 0);
-    int n1[1] = {D};
-    size_t war = 0, wcr = 0;
-    if (cufftMakePlanMany(ar, 1, n1, nullptr, 1, D, nullptr, 1, D / 2 + 1, CUFFT_R2C, B * D, &war) !=
-            CUFFT_SUCCESS ||
-        cufftMakePlanMany(cr, 1, n1, nullptr, 1, D / 2 + 1, nullptr, 1, D, CUFFT_C2R, B * D, &wcr) !=
-            CUFFT_SUCCESS) {
-      cufftDestroy(ar);
-      cufftDestroy(cr);
-      gs_fft_destroy(fft);
-      return GS_ECUDA;
-    }
-    fft->r2c_rows = (int)ar;
-    fft->c2r_rows = (int)cr;
-    if (war > fft->work_bytes) fft->work_bytes = war;
-    if (wcr > fft->work_bytes) fft->work_bytes = wcr;
-  }
   return GS_OK;
 }
 
@@ -211,20 +189,14 @@ int gs_ctf_loss_grad(const gs_config* cfg, const float* Q, const float* Y, const
   float2* specY = ws_ptr<float2>(ws, off);
   float2* specQ = ws_ptr<float2>(ws, off + spec_bytes);
   void* work = ws_ptr<void>(ws, off + 2 * spec_bytes);
-  if (cfg->D == 256 && fft->r2c_rows && fft->c2r_rows) {
-    // rows by cuFFT; column FFTs, the pointwise step and the inverse column FFT in one kernel
-    cufftHandle ar = (cufftHandle)fft->r2c_rows, cr = (cufftHandle)fft->c2r_rows;
-    if (cufftSetStream(ar, s) != CUFFT_SUCCESS || cufftSetStream(cr, s) != CUFFT_SUCCESS) return GS_ECUDA;
-    if (cufftSetWorkArea(ar, work) != CUFFT_SUCCESS || cufftSetWorkArea(cr, work) != CUFFT_SUCCESS)
-      return GS_ECUDA;
-    if (cufftExecR2C(ar, const_cast<float*>(Q), reinterpret_cast<cufftComplex*>(specQ)) != CUFFT_SUCCESS)
-      return GS_ECUDA;
-    if (cufftExecR2C(ar, const_cast<float*>(Y), reinterpret_cast<cufftComplex*>(specY)) != CUFFT_SUCCESS)
-      return GS_ECUDA;
+  if (cfg->D == 256) {
+    // the row transforms (Q and Y in one launch, then the C2R), and the column FFTs, the
+    // pointwise step and the inverse column FFT in one kernel: no cuFFT on this path
+    if (launch_rows_r2c2(Q, Y, specQ, specY, B, s) != cudaSuccess) return GS_ECUDA;
     if (launch_ctf_cols(*cfg, specQ, specY, ctf, B, loss, ws_ptr<void>(ws, off + 2 * spec_bytes + work_bytes), s) !=
         cudaSuccess)
       return GS_ECUDA;
-    if (cufftExecC2R(cr, reinterpret_cast<cufftComplex*>(specQ), dLdQ) != CUFFT_SUCCESS) return GS_ECUDA;
+    if (launch_rows_c2r(specQ, dLdQ, B, s) != cudaSuccess) return GS_ECUDA;
     return GS_OK;
   }
   cufftHandle a = (cufftHandle)fft->r2c, c = (cufftHandle)fft->c2r;

@@ -325,6 +325,116 @@ __global__ void __launch_bounds__(256) k_ctf_cols(float2* __restrict__ qr, const
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Row transforms of the D = 256 training path (the 1-D R2C of Q and Y along x, and the
+// final 1-D C2R), unnormalized like cuFFT's.  A CTA holds 16 complex rows of 256 in shared
+// memory, element n of row j at j * kRowP + n + n / 16 (the padding spreads the 16-strided
+// accesses of the radix-16 steps over the banks), 16 threads per row.
+//   k_rows_r2c2: one complex FFT of Z = Q + iY per row gives both half spectra:
+//                Q^[k] = (Z[k] + conj Z[256 - k]) / 2,  Y^[k] = (Z[k] - conj Z[256 - k]) / 2i.
+//   k_rows_c2r:  one complex FFT per pair of rows: Z = F1 + i F2, F the Hermitian extension of
+//                the row's half spectrum (imaginary parts of the DC and Nyquist terms dropped,
+//                as a C2R transform does), and the rows are Re z and Im z.
+// ---------------------------------------------------------------------------------------
+constexpr int kRowP = kColD + kColD / 16;  // padded row of 272 complex values
+constexpr int kRowsPerCta = 16;
+
+__device__ __forceinline__ int rpos(int n) { return n + (n >> 4); }
+
+// In-place 256-point FFT of the 16 rows held in z (this thread: row j = t >> 4, index s = t & 15).
+template <bool kInv>
+__device__ __forceinline__ void fft256_rows(float2* __restrict__ z, const float2* __restrict__ tw) {
+  const int j = threadIdx.x >> 4, sub = threadIdx.x & 15;
+  float2* a = z + j * kRowP;
+  float2 x[16];
+  // step 1: a 16-point DFT over the coarse index of element 16 n + sub, twiddled
+#pragma unroll
+  for (int n = 0; n < 16; ++n) x[n] = a[rpos(16 * n + sub)];
+  dft16<kInv>(x);
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    float2 v = x[4 * (c & 3) + (c >> 2)];
+    if (c != 0) v = cmul(v, kInv ? conjf2(tw[sub * c]) : tw[sub * c]);
+    a[rpos(16 * c + sub)] = v;
+  }
+  __syncthreads();
+  // step 2: a 16-point DFT over the fine index, for coarse output c = sub
+#pragma unroll
+  for (int n = 0; n < 16; ++n) x[n] = a[rpos(16 * sub + n)];
+  __syncthreads();
+  dft16<kInv>(x);
+#pragma unroll
+  for (int d = 0; d < 16; ++d) a[rpos(sub + 16 * d)] = x[4 * (d & 3) + (d >> 2)];
+  __syncthreads();
+}
+
+__device__ __forceinline__ void row_twiddles(float2* tw) {
+  float sn, cs;
+  sincospif((float)threadIdx.x / 128.f, &sn, &cs);  // w256^m = exp(-2 pi i m / 256)
+  tw[threadIdx.x] = make_float2(cs, -sn);
+}
+
+__global__ void __launch_bounds__(256) k_rows_r2c2(const float* __restrict__ Q, const float* __restrict__ Y,
+                                                   float2* __restrict__ qr, float2* __restrict__ yr) {
+  __shared__ float2 z[kRowsPerCta * kRowP];
+  __shared__ float2 tw[kColD];
+  const size_t r0 = (size_t)blockIdx.x * kRowsPerCta;  // first row of the CTA (rows of all images)
+  const float* q = Q + r0 * kColD;
+  const float* y = Y + r0 * kColD;
+#pragma unroll 4
+  for (int j = 0; j < kRowsPerCta; ++j) {
+    const int n = threadIdx.x;
+    z[j * kRowP + rpos(n)] = make_float2(__ldg(q + j * kColD + n), __ldg(y + j * kColD + n));
+  }
+  row_twiddles(tw);
+  __syncthreads();
+  fft256_rows<false>(z, tw);
+  float2* oq = qr + r0 * kColW2;
+  float2* oy = yr + r0 * kColW2;
+  for (int e = threadIdx.x; e < kRowsPerCta * kColW2; e += blockDim.x) {
+    const int j = e / kColW2, k = e - j * kColW2;
+    const float2 a = z[j * kRowP + rpos(k)], b = conjf2(z[j * kRowP + rpos((kColD - k) & (kColD - 1))]);
+    oq[e] = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y + b.y));
+    oy[e] = make_float2(0.5f * (a.y - b.y), -0.5f * (a.x - b.x));
+  }
+}
+
+__global__ void __launch_bounds__(256) k_rows_c2r(const float2* __restrict__ spec, float* __restrict__ out) {
+  __shared__ float2 z[kRowsPerCta * kRowP];
+  __shared__ float2 tw[kColD];
+  const size_t r0 = (size_t)blockIdx.x * 2 * kRowsPerCta;  // 32 rows, paired into 16 complex rows
+  const float2* g = spec + r0 * kColW2;
+  // pass 1: Z = F1 (the even rows); pass 2: Z += i F2 (the odd rows)
+#pragma unroll
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int e = threadIdx.x; e < kRowsPerCta * kColW2; e += blockDim.x) {
+      const int p = e / kColW2, k = e - p * kColW2;
+      float2 v = g[(size_t)(2 * p + pass) * kColW2 + k];
+      if (k == 0 || k == kColD / 2) v.y = 0.f;
+      float2* a = z + p * kRowP;
+      if (pass == 0) {
+        a[rpos(k)] = v;
+        if (k != 0 && k != kColD / 2) a[rpos(kColD - k)] = conjf2(v);
+      } else {
+        // + i v at k, + i conj(v) at 256 - k
+        a[rpos(k)] = make_float2(a[rpos(k)].x - v.y, a[rpos(k)].y + v.x);
+        if (k != 0 && k != kColD / 2) a[rpos(kColD - k)] = make_float2(a[rpos(kColD - k)].x + v.y, a[rpos(kColD - k)].y + v.x);
+      }
+    }
+    if (pass == 0) row_twiddles(tw);
+    __syncthreads();
+  }
+  fft256_rows<true>(z, tw);
+  float* o = out + r0 * kColD;
+#pragma unroll 4
+  for (int p = 0; p < kRowsPerCta; ++p) {
+    const int n = threadIdx.x;
+    const float2 v = z[p * kRowP + rpos(n)];
+    o[(size_t)(2 * p) * kColD + n] = v.x;
+    o[(size_t)(2 * p + 1) * kColD + n] = v.y;
+  }
+}
+
 // One Adam update (Sec. 4.1; bias corrections c1 = 1 / (1 - b1^t), c2 = 1 / (1 - b2^t)).
 __device__ __forceinline__ void adam_one(float& th, float g, float& m, float& v, float lr, float b1, float b2,
                                          float eps, float c1, float c2) {
@@ -454,6 +564,18 @@ cudaError_t launch_ctf_cols(const gs_config& cfg, float2* qr, const float2* yr, 
   if (e != cudaSuccess) return e;
   const float scale = cfg.reduction == 1 ? 1.f / ((float)cfg.D * (float)cfg.D) : 1.f;
   k_ctf_cols<<<dim3(kColCtas, B), 256, sm, s>>>(qr, yr, ctf, scale, partial, ticket, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rows_r2c2(const float* Q, const float* Y, float2* qr, float2* yr, int B, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  k_rows_r2c2<<<B * kColD / kRowsPerCta, 256, 0, s>>>(Q, Y, qr, yr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rows_c2r(const float2* spec, float* out, int B, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  k_rows_c2r<<<B * kColD / (2 * kRowsPerCta), 256, 0, s>>>(spec, out);
   return cudaGetLastError();
 }
 

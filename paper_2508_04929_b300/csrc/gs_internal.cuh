@@ -138,6 +138,9 @@ cudaError_t launch_render_bwd(const gs_config& cfg, const gs_record* proj, int N
 cudaError_t launch_bwd_finalize(const float* theta, const float* gauss, int N, float* gacc, float* dtheta,
                                 cudaStream_t s);
 cudaError_t launch_ctf_mul(const gs_config& cfg, float2* spec, const float* ctf, int B, cudaStream_t s);
+// Row transforms of the D = 256 training path: the 1-D R2C of Q and Y (one launch), and the 1-D C2R.
+cudaError_t launch_rows_r2c2(const float* Q, const float* Y, float2* qr, float2* yr, int B, cudaStream_t s);
+cudaError_t launch_rows_c2r(const float2* spec, float* out, int B, cudaStream_t s);
 cudaError_t launch_ctf_cols(const gs_config& cfg, float2* qr, const float2* yr, const float* ctf, int B,
                             float* loss, void* red, cudaStream_t s);
 cudaError_t launch_ctf_loss(const gs_config& cfg, float2* specQ, const float2* specY, const float* ctf, int B,
