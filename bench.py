@@ -52,12 +52,12 @@ RENDER_TRAFFIC = {"sha256": "6a4c04e970708d894f77b790d82b11d0ff960c93249a835ab7b
 # libgs kernels launched by one graph-captured training step (cuFFT's and torch's gradient
 # zeroing are library kernels and not counted)
 def step_kernels(D, tile):
-    """The library's kernels that one graph-captured training step launches, once each (the
-    cuFFT row transforms of the D = 256 path and torch's zeroing of the gradient are not ours)."""
+    """The library's kernels that one graph-captured training step launches, once each (cuFFT's
+    2-D transforms at sizes other than 256 and torch's zeroing of the gradient are not ours)."""
     r = "8" if tile == 8 else "16"  # tiles 16 and 32 share the region kernels
+    ctf = ("k_rows_r2c2", "k_ctf_cols", "k_rows_c2r") if D == 256 else ("k_ctf_loss",)
     return ("k_activate", "k_project", "k_bin_count", "k_bin_scan", "k_bin_tiles", "k_bin_base", "k_bin_scatter",
-            "k_render_fwd" + r, "k_ctf_cols" if D == 256 else "k_ctf_loss", "k_render_bwd" + r, "k_bwd_finalize",
-            "k_adam", "k_count_step")
+            "k_render_fwd" + r, *ctf, "k_render_bwd" + r, "k_bwd_finalize", "k_adam", "k_count_step")
 
 
 def parse():
