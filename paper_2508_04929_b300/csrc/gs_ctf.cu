@@ -381,10 +381,16 @@ __global__ void __launch_bounds__(256) k_rows_r2c2(const float* __restrict__ Q, 
   const size_t r0 = (size_t)blockIdx.x * kRowsPerCta;  // first row of the CTA (rows of all images)
   const float* q = Q + r0 * kColD;
   const float* y = Y + r0 * kColD;
-#pragma unroll 4
-  for (int j = 0; j < kRowsPerCta; ++j) {
+  {
+    float vq[kRowsPerCta], vy[kRowsPerCta];  // all 32 loads in flight before the first store
     const int n = threadIdx.x;
-    z[j * kRowP + rpos(n)] = make_float2(__ldg(q + j * kColD + n), __ldg(y + j * kColD + n));
+#pragma unroll
+    for (int j = 0; j < kRowsPerCta; ++j) {
+      vq[j] = __ldg(q + j * kColD + n);
+      vy[j] = __ldg(y + j * kColD + n);
+    }
+#pragma unroll
+    for (int j = 0; j < kRowsPerCta; ++j) z[j * kRowP + rpos(n)] = make_float2(vq[j], vy[j]);
   }
   row_twiddles(tw);
   __syncthreads();
@@ -404,26 +410,18 @@ __global__ void __launch_bounds__(256) k_rows_c2r(const float2* __restrict__ spe
   __shared__ float2 tw[kColD];
   const size_t r0 = (size_t)blockIdx.x * 2 * kRowsPerCta;  // 32 rows, paired into 16 complex rows
   const float2* g = spec + r0 * kColW2;
-  // pass 1: Z = F1 (the even rows); pass 2: Z += i F2 (the odd rows)
-#pragma unroll
-  for (int pass = 0; pass < 2; ++pass) {
-    for (int e = threadIdx.x; e < kRowsPerCta * kColW2; e += blockDim.x) {
-      const int p = e / kColW2, k = e - p * kColW2;
-      float2 v = g[(size_t)(2 * p + pass) * kColW2 + k];
-      if (k == 0 || k == kColD / 2) v.y = 0.f;
-      float2* a = z + p * kRowP;
-      if (pass == 0) {
-        a[rpos(k)] = v;
-        if (k != 0 && k != kColD / 2) a[rpos(kColD - k)] = conjf2(v);
-      } else {
-        // + i v at k, + i conj(v) at 256 - k
-        a[rpos(k)] = make_float2(a[rpos(k)].x - v.y, a[rpos(k)].y + v.x);
-        if (k != 0 && k != kColD / 2) a[rpos(kColD - k)] = make_float2(a[rpos(kColD - k)].x + v.y, a[rpos(kColD - k)].y + v.x);
-      }
-    }
-    if (pass == 0) row_twiddles(tw);
-    __syncthreads();
+  // Z[k] = F1[k] + i F2[k] from rows 2p and 2p + 1, and Z[256 - k] = conj F1[k] + i conj F2[k]
+  for (int e = threadIdx.x; e < kRowsPerCta * kColW2; e += blockDim.x) {
+    const int p = e / kColW2, k = e - p * kColW2;
+    float2 v1 = g[(size_t)(2 * p) * kColW2 + k], v2 = g[(size_t)(2 * p + 1) * kColW2 + k];
+    const bool edge = k == 0 || k == kColD / 2;
+    if (edge) v1.y = v2.y = 0.f;
+    float2* a = z + p * kRowP;
+    a[rpos(k)] = make_float2(v1.x - v2.y, v1.y + v2.x);
+    if (!edge) a[rpos(kColD - k)] = make_float2(v1.x + v2.y, v2.x - v1.y);
   }
+  row_twiddles(tw);
+  __syncthreads();
   fft256_rows<true>(z, tw);
   float* o = out + r0 * kColD;
 #pragma unroll 4
