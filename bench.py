@@ -470,17 +470,15 @@ def main():
     d2h = lossh[0].numel() * 4
     # every step copies its own inputs from pinned host memory (double-buffered: the next
     # step's copy overlaps the current step) and reads its per-image losses back to the host
-    # The step runs as its two graph halves: the front (projection, binning, render) needs only
-    # the poses, so it starts while the step's images are still being copied in.  Each step's
-    # losses come back to pinned host memory; the host reads them one step later, after
-    # enqueueing the next step, so that the GPU never waits for the host.
-    from paper_2508_04929_b300.batched import HostFeeder
-    feeder = HostFeeder(gs)
-    if args.dp:
-        load_front, front, load_back, back = feeder.load, (lambda: None), (lambda: None), step
-    else:
-        gs.record_split()
-        load_front, front, load_back, back = feeder.load_front, gs.replay_front, feeder.load_back, gs.replay_back
+    # Each step's inputs are copied from pinned host memory into one of two input slots of the
+    # graph-captured step while the previous step runs, and the step replays that slot's graphs:
+    # the front half (projection, binning, render) waits only for the poses, so on the first
+    # step it starts while the images are still being copied in.  Each step's losses come back
+    # to pinned host memory; the host reads them one step later, after enqueueing the next
+    # step, so that the GPU never waits for the host.  (The data-parallel step is fed through
+    # the static buffers.)
+    from paper_2508_04929_b300.batched import HostFeeder, SlotFeeder
+    feeder = HostFeeder(gs) if args.dp else SlotFeeder(gs)
     restore()
     done = [torch.cuda.Event(), torch.cuda.Event()]
     host_losses = 0.0
@@ -489,12 +487,14 @@ def main():
     feeder.prefetch(Wh, Ch, Yh)
     pending = None
     for i in range(args.steps):
-        load_front()
+        if args.dp:
+            feeder.load()
         if i + 1 < args.steps:
             feeder.prefetch(Wh, Ch, Yh)
-        front()
-        load_back()
-        back()
+        if args.dp:
+            step()
+        else:
+            feeder.step()
         lossh[i % 2].copy_(prob.sp.loss[: args.B], non_blocking=True)
         done[i % 2].record()
         if pending is not None:
@@ -540,7 +540,7 @@ def main():
             "plain_form": {"value": plain, "unit": UNIT, "form": "one particle per launch sequence, Adam per image"},
             "speedup_vs_plain": (value / world / plain) if plain else None,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "pipelining": "next step's host->device copy overlaps the current step; a step's render starts before its images have arrived; every step's losses are copied back and read by the host one step later"},
+                    "pipelining": "next step's host->device copy (into the other of two input slots of the captured step) overlaps the current step; a step's render starts before its images have arrived; every step's losses are copied back and read by the host one step later"},
             "gpu_launches": len(step_kernels(args.D, tile)) * args.steps,
             "roofline": {"bound": "alu", "kernel": f"k_render_{dom}", "achieved": achieved / 1e9,
                          "peak": peak_exp / 1e9, "unit": "Gex2/s", "frac": achieved / peak_exp,

@@ -78,6 +78,8 @@ class GraphStep:
         self.streams = [torch.cuda.Stream(device=self.dev) for _ in self.problems]
         self.graph = None
         self.graph_front = self.graph_back = None  # recorded on first use
+        self.slot_inputs = None  # [slot][problem] = (W, ctf, Y) for the per-slot graphs
+        self.slot_graphs = None  # [slot] = (front, back)
         self._size_pairs()
         self._record()
 
@@ -138,6 +140,8 @@ class GraphStep:
             p.theta.copy_(th); p.m.copy_(m); p.v.copy_(v); p.t.copy_(t)
         self.graph = self._capture(None)
         self.graph_front = self.graph_back = None
+        if self.slot_graphs is not None:
+            self.record_slots(len(self.slot_graphs))
 
     def _capture(self, part):
         g = torch.cuda.CUDAGraph()
@@ -153,6 +157,28 @@ class GraphStep:
             return
         self.graph_front = self._capture(self._front)
         self.graph_back = self._capture(self._back)
+
+    def record_slots(self, n=2):
+        """Record the step's two halves once per input slot: slot k's graphs read poses, CTF
+        parameters and images from their own buffers ``slot_inputs[k][problem]``, so that a
+        feeder can copy a later step's inputs straight into another slot while this one runs
+        (no device-to-device copy into the static buffers)."""
+        if not self.use_graph:
+            raise RuntimeError("input slots need the graph-captured step")
+        if self.slot_inputs is None or len(self.slot_inputs) != n:
+            self.slot_inputs = [[tuple(torch.empty_like(x) for x in (p.W, p.ctf, p.Y)) for p in self.problems]
+                                for _ in range(n)]
+        static = [(p.W, p.ctf, p.Y) for p in self.problems]
+        graphs = []
+        try:
+            for k in range(n):
+                for p, (W, ctf, Y) in zip(self.problems, self.slot_inputs[k]):
+                    p.W, p.ctf, p.Y = W, ctf, Y
+                graphs.append((self._capture(self._front), self._capture(self._back)))
+        finally:
+            for p, (W, ctf, Y) in zip(self.problems, static):
+                p.W, p.ctf, p.Y = W, ctf, Y
+        self.slot_graphs = graphs
 
     # -- use -------------------------------------------------------------------------------
     def load(self, i, W=None, ctf=None, Y=None):
@@ -170,8 +196,12 @@ class GraphStep:
             self._run_all()
         return [p.sp.loss[: p.B] for p in self.problems]
 
-    def replay_front(self):
-        """The first half of a step (projection, binning, render); reads theta and W."""
+    def replay_front(self, slot=None):
+        """The first half of a step (projection, binning, render); reads theta and W (those of
+        input slot ``slot`` when given)."""
+        if slot is not None:
+            self.slot_graphs[slot][0].replay()
+            return
         if not self.use_graph:
             self._run_all(self._front)
             return
@@ -179,10 +209,12 @@ class GraphStep:
             self.record_split()
         self.graph_front.replay()
 
-    def replay_back(self):
-        """The second half (CTF, loss, backward, Adam); reads ctf and Y.  Returns the
-        per-image loss tensors (device)."""
-        if not self.use_graph:
+    def replay_back(self, slot=None):
+        """The second half (CTF, loss, backward, Adam); reads ctf and Y (those of input slot
+        ``slot`` when given).  Returns the per-image loss tensors (device)."""
+        if slot is not None:
+            self.slot_graphs[slot][1].replay()
+        elif not self.use_graph:
             self._run_all(self._back)
         else:
             if self.graph_back is None:
@@ -276,3 +308,65 @@ class HostFeeder:
         self.gs.load(self.i, Y=self.bufs[j][2])
         self.free[j].record(cur)
         self.used += 1
+
+
+class SlotFeeder:
+    """Feeding of a single-problem GraphStep through its input slots (``record_slots``): each
+    step's pinned host inputs are copied straight into the slot its graphs read, on side
+    streams, while earlier steps run, and ``step()`` replays the slot's two halves.  The front
+    half waits only for the poses and CTF parameters, the back half for the images; no input
+    is copied again on the device."""
+
+    def __init__(self, gs: GraphStep, copy_streams=4):
+        if len(gs.problems) != 1:
+            raise ValueError("SlotFeeder drives a GraphStep of one problem")
+        if gs.slot_graphs is None:
+            gs.record_slots(2)
+        self.gs = gs
+        self.n = len(gs.slot_graphs)
+        dev = gs.problems[0].theta.device
+        self.copy_streams = [torch.cuda.Stream(device=dev) for _ in range(max(1, copy_streams))]
+        self.ready_small = [torch.cuda.Event() for _ in range(self.n)]  # W and ctf of the slot
+        self.ready = [torch.cuda.Event() for _ in range(self.n)]        # ... and its images
+        self.free = [torch.cuda.Event() for _ in range(self.n)]         # its last step has run
+        self.filled = 0
+        self.used = 0
+
+    def prefetch(self, W, ctf, Y):
+        """Start copying one step's pinned host inputs (W[B, 9], ctf[B, 5], Y[B, D, D]) into the
+        next free slot.  At most ``n`` steps may be prefetched ahead of ``step()``."""
+        if self.filled - self.used >= self.n:
+            raise RuntimeError("every input slot holds a step that has not run yet")
+        j = self.filled % self.n
+        dW, dc, dY = self.gs.slot_inputs[j][0]
+        main = self.copy_streams[0]
+        main.wait_event(self.free[j])
+        with torch.cuda.stream(main):
+            dW.copy_(W, non_blocking=True)
+            dc.copy_(ctf, non_blocking=True)
+            self.ready_small[j].record(main)
+        parts = list(zip(dY.chunk(len(self.copy_streams)), Y.chunk(len(self.copy_streams))))
+        for s, (dst, src) in zip(self.copy_streams, parts):
+            if s is not main:
+                s.wait_stream(main)
+            with torch.cuda.stream(s):
+                dst.copy_(src, non_blocking=True)
+        for s in self.copy_streams[1:len(parts)]:
+            main.wait_stream(s)
+        self.ready[j].record(main)
+        self.filled += 1
+
+    def step(self):
+        """Run the oldest prefetched step (stream-ordered).  Returns the per-image losses
+        (device)."""
+        if self.used >= self.filled:
+            raise RuntimeError("no prefetched step")
+        j = self.used % self.n
+        cur = torch.cuda.current_stream()
+        cur.wait_event(self.ready_small[j])
+        self.gs.replay_front(j)
+        cur.wait_event(self.ready[j])
+        loss = self.gs.replay_back(j)
+        self.free[j].record(cur)
+        self.used += 1
+        return loss

@@ -17,7 +17,7 @@ from paper_2508_04929_b300 import build  # noqa: E402
 
 build.build()
 from paper_2508_04929_b300 import _lib as L  # noqa: E402
-from paper_2508_04929_b300.batched import GraphStep, HostFeeder, Problem  # noqa: E402
+from paper_2508_04929_b300.batched import GraphStep, HostFeeder, Problem, SlotFeeder  # noqa: E402
 from paper_2508_04929_b300.splat import Splatter  # noqa: E402
 
 GROUPS = (slice(0, 3), slice(3, 6), slice(6, 10), slice(10, 11))
@@ -164,6 +164,37 @@ def test_host_feeder_halves_match_whole_loads():
     for x, y in zip(whole, halves):
         assert torch.equal(x, y)
     assert not torch.equal(whole[0], whole[1])  # the steps did take new inputs
+    gs.close()
+
+
+def test_slot_feeder_matches_host_feeder():
+    """Steps fed through the graph's input slots (host copies straight into the buffers the
+    slot's graphs read) give the losses of steps fed through the static buffers, step after
+    step, and the slot graphs are re-recorded when an overflow re-sizes the pair buffer."""
+    p, _ = _problem(66, 40, 400, 4)
+    gs = GraphStep([p], adam=False)
+    rng = synth.rng_for(67)
+    batches = [(torch.from_numpy(synth.random_poses(4, rng).reshape(4, 9)).pin_memory(),
+                torch.from_numpy(synth.random_ctf(4, rng)).pin_memory(),
+                torch.from_numpy(synth.smooth_field(4, 40, rng, scale=100.0)).pin_memory()) for _ in range(4)]
+    ref = []
+    fa = HostFeeder(gs)
+    for i in range(4):
+        fa.prefetch(*batches[i])
+        fa.load()
+        ref.append(gs.replay()[0].clone())
+    sf = SlotFeeder(gs)
+    got = []
+    sf.prefetch(*batches[0])
+    for i in range(4):
+        if i + 1 < 4:
+            sf.prefetch(*batches[i + 1])
+        got.append(sf.step()[0].clone())
+    torch.cuda.synchronize()
+    for x, y in zip(ref, got):
+        assert torch.equal(x, y)
+    with pytest.raises(RuntimeError):
+        sf.step()  # nothing prefetched
     gs.close()
 
 
