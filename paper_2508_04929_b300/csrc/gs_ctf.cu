@@ -327,7 +327,8 @@ __global__ void __launch_bounds__(256) k_ctf_cols(float2* __restrict__ qr, const
 
 // ---------------------------------------------------------------------------------------
 // Row transforms of the D = 256 training path (the 1-D R2C of Q and Y along x, and the
-// final 1-D C2R), unnormalized like cuFFT's.  A CTA holds 16 complex rows of 256 in shared
+// final 1-D C2R: the x half of the 2-D transforms of App. A.2 Eq. 14), unnormalized like
+// cuFFT's.  A CTA holds 16 complex rows of 256 in shared
 // memory, element n of row j at j * kRowP + n + n / 16 (the padding spreads the 16-strided
 // accesses of the radix-16 steps over the banks), 16 threads per row.
 //   k_rows_r2c2: one complex FFT of Z = Q + iY per row gives both half spectra:
