@@ -114,6 +114,32 @@ def max_over_ranks(x, dist=None, device="cpu"):
     return float(t.item())
 
 
+def measure_h2d(torch, host, dev, reps=5):
+    """Pinned host -> device bandwidth of this machine (GB/s) for one step's images, copied in four
+    chunks on four streams as the feeders do; the end-to-end rate cannot exceed B images per
+    step's copy time."""
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    cur = torch.cuda.current_stream()
+
+    def once():
+        for s, d, h in zip(streams, dev.chunk(4), host.chunk(4)):
+            s.wait_stream(cur)
+            with torch.cuda.stream(s):
+                d.copy_(h, non_blocking=True)
+        for s in streams:
+            cur.wait_stream(s)
+
+    once()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        once()
+    e1.record()
+    torch.cuda.synchronize()
+    return reps * host.numel() * host.element_size() / (e0.elapsed_time(e1) * 1e-3) / 1e9
+
+
 def make_inputs(args, seed=0):
     rng = synth.rng_for(seed)
     th = synth.random_gaussians(args.N, args.D, rng)
@@ -504,6 +530,7 @@ def main():
     done[pending].synchronize()
     host_losses += float(lossh[pending].sum())
     e2e = world * args.B * args.steps / (time.perf_counter() - s0)
+    h2d_gbps = measure_h2d(torch, Yh, prob.Y)
     torch.cuda.synchronize()
     gs.close()
 
@@ -540,6 +567,7 @@ def main():
             "plain_form": {"value": plain, "unit": UNIT, "form": "one particle per launch sequence, Adam per image"},
             "speedup_vs_plain": (value / world / plain) if plain else None,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "h2d_GBps": h2d_gbps, "h2d_bound": world * args.B / (h2d / (h2d_gbps * 1e9)),
                     "pipelining": "next step's host->device copy (into the other of two input slots of the captured step) overlaps the current step; a step's render starts before its images have arrived; every step's losses are copied back and read by the host one step later"},
             "gpu_launches": len(step_kernels(args.D, tile)) * args.steps,
             "roofline": {"bound": "alu", "kernel": f"k_render_{dom}", "achieved": achieved / 1e9,
