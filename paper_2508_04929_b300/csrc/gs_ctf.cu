@@ -342,15 +342,15 @@ constexpr int kRowsPerCta = 16;
 
 __device__ __forceinline__ int rpos(int n) { return n + (n >> 4); }
 
-// In-place 256-point FFT of the 16 rows held in z (this thread: row j = t >> 4, index s = t & 15).
+// 256-point FFT of the 16 rows of z (this thread: row j = t >> 4, index sub = t & 15), in two
+// radix-16 steps.  Step 1 takes x[n] = element 16 n + sub of the row (from wherever the caller
+// read it), DFTs over n, twiddles and stores to z; step 2 DFTs over the fine index and leaves
+// X[sub + 16 d] in x[4 (d & 3) + (d >> 2)].
 template <bool kInv>
-__device__ __forceinline__ void fft256_rows(float2* __restrict__ z, const float2* __restrict__ tw) {
+__device__ __forceinline__ void fft256_rows_step1(float2 (&x)[16], float2* __restrict__ z,
+                                                  const float2* __restrict__ tw) {
   const int j = threadIdx.x >> 4, sub = threadIdx.x & 15;
   float2* a = z + j * kRowP;
-  float2 x[16];
-  // step 1: a 16-point DFT over the coarse index of element 16 n + sub, twiddled
-#pragma unroll
-  for (int n = 0; n < 16; ++n) x[n] = a[rpos(16 * n + sub)];
   dft16<kInv>(x);
 #pragma unroll
   for (int c = 0; c < 16; ++c) {
@@ -358,15 +358,15 @@ __device__ __forceinline__ void fft256_rows(float2* __restrict__ z, const float2
     if (c != 0) v = cmul(v, kInv ? conjf2(tw[sub * c]) : tw[sub * c]);
     a[rpos(16 * c + sub)] = v;
   }
-  __syncthreads();
-  // step 2: a 16-point DFT over the fine index, for coarse output c = sub
+}
+
+template <bool kInv>
+__device__ __forceinline__ void fft256_rows_step2(float2 (&x)[16], const float2* __restrict__ z) {
+  const int j = threadIdx.x >> 4, sub = threadIdx.x & 15;
+  const float2* a = z + j * kRowP;
 #pragma unroll
   for (int n = 0; n < 16; ++n) x[n] = a[rpos(16 * sub + n)];
-  __syncthreads();
   dft16<kInv>(x);
-#pragma unroll
-  for (int d = 0; d < 16; ++d) a[rpos(sub + 16 * d)] = x[4 * (d & 3) + (d >> 2)];
-  __syncthreads();
 }
 
 __device__ __forceinline__ void row_twiddles(float2* tw) {
@@ -380,22 +380,21 @@ __global__ void __launch_bounds__(256) k_rows_r2c2(const float* __restrict__ Q, 
   __shared__ float2 z[kRowsPerCta * kRowP];
   __shared__ float2 tw[kColD];
   const size_t r0 = (size_t)blockIdx.x * kRowsPerCta;  // first row of the CTA (rows of all images)
-  const float* q = Q + r0 * kColD;
-  const float* y = Y + r0 * kColD;
-  {
-    float vq[kRowsPerCta], vy[kRowsPerCta];  // all 32 loads in flight before the first store
-    const int n = threadIdx.x;
+  const int j = threadIdx.x >> 4, sub = threadIdx.x & 15;
+  const float* q = Q + (r0 + j) * kColD + sub;
+  const float* y = Y + (r0 + j) * kColD + sub;
+  float2 x[16];
 #pragma unroll
-    for (int j = 0; j < kRowsPerCta; ++j) {
-      vq[j] = __ldg(q + j * kColD + n);
-      vy[j] = __ldg(y + j * kColD + n);
-    }
-#pragma unroll
-    for (int j = 0; j < kRowsPerCta; ++j) z[j * kRowP + rpos(n)] = make_float2(vq[j], vy[j]);
-  }
+  for (int n = 0; n < 16; ++n) x[n] = make_float2(__ldg(q + 16 * n), __ldg(y + 16 * n));  // 64-byte runs
   row_twiddles(tw);
   __syncthreads();
-  fft256_rows<false>(z, tw);
+  fft256_rows_step1<false>(x, z, tw);
+  __syncthreads();
+  fft256_rows_step2<false>(x, z);
+  __syncthreads();
+#pragma unroll
+  for (int d = 0; d < 16; ++d) z[j * kRowP + rpos(sub + 16 * d)] = x[4 * (d & 3) + (d >> 2)];
+  __syncthreads();
   float2* oq = qr + r0 * kColW2;
   float2* oy = yr + r0 * kColW2;
   for (int e = threadIdx.x; e < kRowsPerCta * kColW2; e += blockDim.x) {
@@ -423,14 +422,22 @@ __global__ void __launch_bounds__(256) k_rows_c2r(const float2* __restrict__ spe
   }
   row_twiddles(tw);
   __syncthreads();
-  fft256_rows<true>(z, tw);
-  float* o = out + r0 * kColD;
-#pragma unroll 4
-  for (int p = 0; p < kRowsPerCta; ++p) {
-    const int n = threadIdx.x;
-    const float2 v = z[p * kRowP + rpos(n)];
-    o[(size_t)(2 * p) * kColD + n] = v.x;
-    o[(size_t)(2 * p + 1) * kColD + n] = v.y;
+  const int j = threadIdx.x >> 4, sub = threadIdx.x & 15;
+  float2 x[16];
+#pragma unroll
+  for (int n = 0; n < 16; ++n) x[n] = z[j * kRowP + rpos(16 * n + sub)];
+  __syncthreads();
+  fft256_rows_step1<true>(x, z, tw);
+  __syncthreads();
+  fft256_rows_step2<true>(x, z);
+  // element sub + 16 d of complex row j: real part to row 2 j, imaginary part to row 2 j + 1
+  float* o0 = out + (r0 + 2 * j) * kColD + sub;
+  float* o1 = o0 + kColD;
+#pragma unroll
+  for (int d = 0; d < 16; ++d) {
+    const float2 v = x[4 * (d & 3) + (d >> 2)];
+    o0[16 * d] = v.x;
+    o1[16 * d] = v.y;
   }
 }
 
