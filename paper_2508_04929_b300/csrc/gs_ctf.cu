@@ -243,6 +243,34 @@ __device__ __forceinline__ void fft256_cols(float2* __restrict__ a, const float2
   __syncthreads();
 }
 
+// Step 1 of fft256_cols with the thread's inputs already in registers: x[n] = element
+// 16 n + sub of column j (the rows this thread loaded).
+template <bool kInv>
+__device__ __forceinline__ void fft256_cols_step1(float2 (&x)[16], float2* __restrict__ a,
+                                                  const float2* __restrict__ tw) {
+  const int j = threadIdx.x & 15, sub = threadIdx.x >> 4;
+  dft16<kInv>(x);
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    float2 v = x[4 * (c & 3) + (c >> 2)];
+    if (c != 0) v = cmul(v, kInv ? conjf2(tw[sub * c]) : tw[sub * c]);
+    a[(16 * c + sub) * kColNC + j] = v;
+  }
+}
+
+// Step 2 of fft256_cols (after a barrier that follows step 1).
+template <bool kInv>
+__device__ __forceinline__ void fft256_cols_step2(float2* __restrict__ a) {
+  const int j = threadIdx.x & 15, sub = threadIdx.x >> 4;
+  float2 x[16];
+#pragma unroll
+  for (int n = 0; n < 16; ++n) x[n] = a[(16 * sub + n) * kColNC + j];
+  __syncthreads();
+  dft16<kInv>(x);
+#pragma unroll
+  for (int d = 0; d < 16; ++d) a[(sub + 16 * d) * kColNC + j] = x[4 * (d & 3) + (d >> 2)];
+}
+
 __global__ void __launch_bounds__(256) k_ctf_cols(float2* __restrict__ qr, const float2* __restrict__ yr,
                                                   const float* __restrict__ ctf, float scale,
                                                   float* __restrict__ partial, unsigned* __restrict__ ticket,
@@ -258,19 +286,20 @@ __global__ void __launch_bounds__(256) k_ctf_cols(float2* __restrict__ qr, const
   const int b = blockIdx.y, c0 = blockIdx.x * kColNC;
   const int j = threadIdx.x & 15, sub = threadIdx.x >> 4;
   const bool col = c0 + j < kColW2;
+  // rows sub + 16 r of column j: exactly this thread's inputs to step 1 of both column FFTs
+  const size_t img = (size_t)b * kColD * kColW2;
+  float2 xq[16], xy[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const size_t gi = img + (size_t)(sub + 16 * r) * kColW2 + c0 + j;
+    xq[r] = col ? qr[gi] : make_float2(0.f, 0.f);
+    xy[r] = col ? yr[gi] : make_float2(0.f, 0.f);
+  }
   if (threadIdx.x == 0) ctf_constants(ctf, b, kColD, cst);
   {
     float sn, cs;
     sincospif((float)threadIdx.x / 128.f, &sn, &cs);  // w256^m = exp(-2 pi i m / 256)
     tw[threadIdx.x] = make_float2(cs, -sn);
-  }
-  const size_t img = (size_t)b * kColD * kColW2;
-#pragma unroll 4
-  for (int r = 0; r < 16; ++r) {
-    const int y = sub + 16 * r;
-    const size_t gi = img + (size_t)y * kColW2 + c0 + j;
-    aq[y * kColNC + j] = col ? qr[gi] : make_float2(0.f, 0.f);
-    ay[y * kColNC + j] = col ? yr[gi] : make_float2(0.f, 0.f);
   }
   __syncthreads();
   {
@@ -280,8 +309,12 @@ __global__ void __launch_bounds__(256) k_ctf_cols(float2* __restrict__ qr, const
       Hs[e] = ctf_value_n((float)(ky * ky + kx * kx), c);
     }
   }
-  fft256_cols<false>(aq, tw);
-  fft256_cols<false>(ay, tw);
+  fft256_cols_step1<false>(xq, aq, tw);
+  fft256_cols_step1<false>(xy, ay, tw);
+  __syncthreads();
+  fft256_cols_step2<false>(aq);
+  fft256_cols_step2<false>(ay);
+  __syncthreads();
   const float inv_d2 = 1.f / ((float)kColD * (float)kColD);
   const float gscale = 2.f * scale * inv_d2;
   const int kx = c0 + j;
