@@ -216,35 +216,10 @@ __device__ __forceinline__ void dft16(float2 (&x)[16]) {
   for (int k1 = 0; k1 < 4; ++k1) dft4<kInv>(x[4 * k1], x[4 * k1 + 1], x[4 * k1 + 2], x[4 * k1 + 3]);
 }
 
-// 256-point FFT along the rows of a [256][16] shared array, one column per 16 threads
-// (thread: column j = t & 15, sub = t >> 4).  tw[m] = w256^m; kInv uses the conjugates.
-template <bool kInv>
-__device__ __forceinline__ void fft256_cols(float2* __restrict__ a, const float2* __restrict__ tw) {
-  const int j = threadIdx.x & 15, sub = threadIdx.x >> 4;
-  float2 x[16];
-  // step 1 (this thread's fine index b = sub): a 16-point DFT over the coarse index, twiddled
-#pragma unroll
-  for (int n = 0; n < 16; ++n) x[n] = a[(16 * n + sub) * kColNC + j];
-  dft16<kInv>(x);
-#pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    float2 v = x[4 * (c & 3) + (c >> 2)];
-    if (c != 0) v = cmul(v, kInv ? conjf2(tw[sub * c]) : tw[sub * c]);
-    a[(16 * c + sub) * kColNC + j] = v;
-  }
-  __syncthreads();
-  // step 2 (this thread's c = sub): a 16-point DFT over the fine index
-#pragma unroll
-  for (int n = 0; n < 16; ++n) x[n] = a[(16 * sub + n) * kColNC + j];
-  __syncthreads();
-  dft16<kInv>(x);
-#pragma unroll
-  for (int d = 0; d < 16; ++d) a[(sub + 16 * d) * kColNC + j] = x[4 * (d & 3) + (d >> 2)];
-  __syncthreads();
-}
-
-// Step 1 of fft256_cols with the thread's inputs already in registers: x[n] = element
-// 16 n + sub of column j (the rows this thread loaded).
+// 256-point FFT down the 16 columns of a [256][16] shared array in two radix-16 steps
+// (thread: column j = t & 15, index sub = t >> 4; tw[m] = w256^m, kInv uses the conjugates).
+// Step 1 takes x[n] = element 16 n + sub of column j (the rows this thread loaded), DFTs over
+// n, twiddles and stores to a.
 template <bool kInv>
 __device__ __forceinline__ void fft256_cols_step1(float2 (&x)[16], float2* __restrict__ a,
                                                   const float2* __restrict__ tw) {
@@ -258,17 +233,15 @@ __device__ __forceinline__ void fft256_cols_step1(float2 (&x)[16], float2* __res
   }
 }
 
-// Step 2 of fft256_cols (after a barrier that follows step 1).
+// Step 2 (after a barrier that follows step 1) DFTs over the fine index, the result kept in registers:
+// X[sub + 16 d] of column j in x[4 (d & 3) + (d >> 2)], the rows sub + 16 d that this thread
+// also loaded.
 template <bool kInv>
-__device__ __forceinline__ void fft256_cols_step2(float2* __restrict__ a) {
+__device__ __forceinline__ void fft256_cols_step2(float2 (&x)[16], const float2* __restrict__ a) {
   const int j = threadIdx.x & 15, sub = threadIdx.x >> 4;
-  float2 x[16];
 #pragma unroll
   for (int n = 0; n < 16; ++n) x[n] = a[(16 * sub + n) * kColNC + j];
-  __syncthreads();
   dft16<kInv>(x);
-#pragma unroll
-  for (int d = 0; d < 16; ++d) a[(sub + 16 * d) * kColNC + j] = x[4 * (d & 3) + (d >> 2)];
 }
 
 __global__ void __launch_bounds__(256) k_ctf_cols(float2* __restrict__ qr, const float2* __restrict__ yr,
@@ -312,30 +285,34 @@ __global__ void __launch_bounds__(256) k_ctf_cols(float2* __restrict__ qr, const
   fft256_cols_step1<false>(xq, aq, tw);
   fft256_cols_step1<false>(xy, ay, tw);
   __syncthreads();
-  fft256_cols_step2<false>(aq);
-  fft256_cols_step2<false>(ay);
-  __syncthreads();
+  // From here each thread works on rows sub + 16 r of column j in registers: the forward FFTs'
+  // outputs, the pointwise step and the inverse FFT's inputs are the same rows.
+  fft256_cols_step2<false>(xq, aq);
+  fft256_cols_step2<false>(xy, ay);
   const float inv_d2 = 1.f / ((float)kColD * (float)kColD);
   const float gscale = 2.f * scale * inv_d2;
   const int kx = c0 + j;
   const float wgt = (kx == 0 || 2 * kx == kColD) ? 1.f : 2.f;
   float acc = 0.f;
-#pragma unroll 4
+  float2 xg[16];  // the adjoint G at row 16 n + sub, the inverse FFT's step-1 input
+#pragma unroll
   for (int r = 0; r < 16; ++r) {
-    const int ky = sub + 16 * r;
+    const int ky = sub + 16 * r, p = 4 * (r & 3) + (r >> 2);
     const float H = Hs[(ky <= kColD / 2 ? ky : kColD - ky) * kColNC + j];
-    const float2 qv = aq[ky * kColNC + j], yv = ay[ky * kColNC + j];
+    const float2 qv = xq[p], yv = xy[p];
     const float zx = fmaf(H, qv.x, -yv.x), zy = fmaf(H, qv.y, -yv.y);
     if (col) acc = fmaf(wgt, fmaf(zx, zx, zy * zy), acc);
     const float gH = gscale * H;
-    aq[ky * kColNC + j] = make_float2(gH * zx, gH * zy);
+    xg[r] = make_float2(gH * zx, gH * zy);
   }
+  __syncthreads();  // every thread has read its step-2 inputs from aq before it is overwritten
+  fft256_cols_step1<true>(xg, aq, tw);
   __syncthreads();
-  fft256_cols<true>(aq, tw);
-#pragma unroll 4
-  for (int r = 0; r < 16; ++r) {
-    const int y = sub + 16 * r;
-    if (col) qr[img + (size_t)y * kColW2 + c0 + j] = aq[y * kColNC + j];
+  fft256_cols_step2<true>(xg, aq);
+#pragma unroll
+  for (int d = 0; d < 16; ++d) {
+    const int y = sub + 16 * d;
+    if (col) qr[img + (size_t)y * kColW2 + c0 + j] = xg[4 * (d & 3) + (d >> 2)];
   }
   // loss: this CTA's sum, then the image's last CTA adds the CTAs' sums in order
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
