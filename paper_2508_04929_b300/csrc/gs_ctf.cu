@@ -401,17 +401,24 @@ __global__ void __launch_bounds__(256) k_rows_r2c2(const float* __restrict__ Q, 
   fft256_rows_step1<false>(x, z, tw);
   __syncthreads();
   fft256_rows_step2<false>(x, z);
-  __syncthreads();
+  // Z[k], k = sub + 16 d, is in this thread; Z[256 - k] is element 15 - d of lane 16 - sub of
+  // the same half-warp (its own element (16 - d) mod 16 for sub = 0)
+  float2* oq = qr + (r0 + j) * kColW2 + sub;
+  float2* oy = yr + (r0 + j) * kColW2 + sub;
+  const int partner = (16 - sub) & 15;
 #pragma unroll
-  for (int d = 0; d < 16; ++d) z[j * kRowP + rpos(sub + 16 * d)] = x[4 * (d & 3) + (d >> 2)];
-  __syncthreads();
-  float2* oq = qr + r0 * kColW2;
-  float2* oy = yr + r0 * kColW2;
-  for (int e = threadIdx.x; e < kRowsPerCta * kColW2; e += blockDim.x) {
-    const int j = e / kColW2, k = e - j * kColW2;
-    const float2 a = z[j * kRowP + rpos(k)], b = conjf2(z[j * kRowP + rpos((kColD - k) & (kColD - 1))]);
-    oq[e] = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y + b.y));
-    oy[e] = make_float2(0.5f * (a.y - b.y), -0.5f * (a.x - b.x));
+  for (int d = 0; d <= 8; ++d) {
+    const float2 a = x[4 * (d & 3) + (d >> 2)];
+    const float2 send = x[4 * ((15 - d) & 3) + ((15 - d) >> 2)];
+    const int ds = (16 - d) & 15;
+    const float2 self = x[4 * (ds & 3) + (ds >> 2)];
+    float2 b = make_float2(__shfl_sync(0xffffffffu, send.x, partner, 16), __shfl_sync(0xffffffffu, send.y, partner, 16));
+    if (sub == 0) b = self;
+    b = conjf2(b);
+    if (d < 8 || sub == 0) {  // k <= 128
+      oq[16 * d] = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y + b.y));
+      oy[16 * d] = make_float2(0.5f * (a.y - b.y), -0.5f * (a.x - b.x));
+    }
   }
 }
 
@@ -419,23 +426,22 @@ __global__ void __launch_bounds__(256) k_rows_c2r(const float2* __restrict__ spe
   __shared__ float2 z[kRowsPerCta * kRowP];
   __shared__ float2 tw[kColD];
   const size_t r0 = (size_t)blockIdx.x * 2 * kRowsPerCta;  // 32 rows, paired into 16 complex rows
-  const float2* g = spec + r0 * kColW2;
-  // Z[k] = F1[k] + i F2[k] from rows 2p and 2p + 1, and Z[256 - k] = conj F1[k] + i conj F2[k]
-  for (int e = threadIdx.x; e < kRowsPerCta * kColW2; e += blockDim.x) {
-    const int p = e / kColW2, k = e - p * kColW2;
-    float2 v1 = g[(size_t)(2 * p) * kColW2 + k], v2 = g[(size_t)(2 * p + 1) * kColW2 + k];
-    const bool edge = k == 0 || k == kColD / 2;
-    if (edge) v1.y = v2.y = 0.f;
-    float2* a = z + p * kRowP;
-    a[rpos(k)] = make_float2(v1.x - v2.y, v1.y + v2.x);
-    if (!edge) a[rpos(kColD - k)] = make_float2(v1.x + v2.y, v2.x - v1.y);
-  }
-  row_twiddles(tw);
-  __syncthreads();
   const int j = threadIdx.x >> 4, sub = threadIdx.x & 15;
+  // step-1 inputs straight from the half spectra of rows 2 j and 2 j + 1:
+  // Z[k] = F1[k] + i F2[k] for k <= 128, and Z[k] = conj F1[256 - k] + i conj F2[256 - k] above
+  const float2* g1 = spec + (r0 + 2 * j) * kColW2;
+  const float2* g2 = g1 + kColW2;
   float2 x[16];
 #pragma unroll
-  for (int n = 0; n < 16; ++n) x[n] = z[j * kRowP + rpos(16 * n + sub)];
+  for (int n = 0; n < 16; ++n) {
+    const int k = 16 * n + sub;
+    const bool lower = k <= kColD / 2;
+    const int m = lower ? k : kColD - k;
+    float2 v1 = g1[m], v2 = g2[m];
+    if (k == 0 || k == kColD / 2) v1.y = v2.y = 0.f;
+    x[n] = lower ? make_float2(v1.x - v2.y, v1.y + v2.x) : make_float2(v1.x + v2.y, v2.x - v1.y);
+  }
+  row_twiddles(tw);
   __syncthreads();
   fft256_rows_step1<true>(x, z, tw);
   __syncthreads();
