@@ -67,14 +67,22 @@ typedef struct gs_config {
   int reduction;      /* loss per image: 0 = sum of squares (Sec. 3.3.5), 1 = mean over pixels */
 } gs_config;
 
-/* Projected record of one (particle, Gaussian) pair: 32 bytes, 16-byte aligned.
- * The splat value at pixel (i, j) is w * 2^(ca dx^2 + cb dx dy + cc dy^2) with
- * dx = j - cx, dy = i - cy (pixel units); w = A / (2 pi sqrt(det Sigma~)) in model units.
+/* Projected record of one (particle, Gaussian) pair: 32 bytes, 16-byte aligned.  With
+ * dx = j - cx, dy = i - cy the offsets of pixel (i, j) from the splat centre (pixel units) and
+ * Sigma~ the 2 x 2 covariance in pixel units (Sxy its world off-diagonal entry), the splat
+ * value there is App. A.2 Eq. 12's normalized 2-D Gaussian w exp(-1/2 d^T Sigma~^-1 d),
+ * w = A / (2 pi sqrt(det Sigma~)) in model units, stored in one of two forms:
+ *   c1 < 0 (well-conditioned): w 2^(c1 dx^2 + c2 dx dy + c3 dy^2), the expanded form with
+ *     (c1, c2, c3) = -log2(e) / (2 det) (Syy, 2 Sxy, Sxx), and c4 = w;
+ *   c1 > 0 (ill-conditioned: c1 > 3, a conditional standard deviation below 0.49 px, or
+ *     (Sxx + Syy)^2 > 100 det, a condition number above about 100):
+ *     2^(c4 - c1 (dx + c2 dy)^2 + c3 dy^2), the completed square with c1 = log2(e)/2 Syy/det,
+ *     c2 = Sxy/Syy, c3 = -log2(e)/2 / Syy, and c4 = log2 w; its centre is refined by the low
+ *     parts that follow the box plane (gs_proj_size).
  * [x0, x1] x [y0, y1] is the clipped support box (empty when x0 > x1). */
 typedef struct gs_record {
   float cx, cy;
-  float ca, cb, cc;
-  float w;
+  float c1, c2, c3, c4;
   int16_t x0, x1, y0, y1;
 } gs_record;
 
@@ -99,9 +107,13 @@ int gs_tiles_per_image(const gs_config* cfg, int* n);
 /* Bytes of the projection buffer that gs_project fills for B particles and N Gaussians:
  * the B*N records (gs_record, particle-major), then, at byte offset 32*B*N, the B*N
  * support boxes again as int32 pairs {x0 | x1 << 16, y0 | y1 << 16} (8 bytes each,
- * particle-major, the same values as the records' boxes).  The binning calls read the
- * boxes from that plane, a quarter of the bytes of the records.  GS_EINVAL if B or N is
- * negative. */
+ * particle-major, the same values as the records' boxes), then, at byte offset 40*B*N, B*N
+ * float pairs (cx_lo, cy_lo): for an ill-conditioned record (c1 > 0, see gs_record), the
+ * centre's low parts -- the centre computed in FP64 from the FP32 pose and mean, minus
+ * (cx, cy) -- which the render calls add to the record's centre; for other records that
+ * pair is not written.  The binning
+ * calls read the boxes from the box plane, a quarter of the bytes of the records.
+ * GS_EINVAL if B or N is negative. */
 int gs_proj_size(int B, int N, size_t* bytes);
 
 /* Workspace bytes for batches of up to B particles and N Gaussians with the given cuFFT

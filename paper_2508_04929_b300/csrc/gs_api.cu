@@ -46,7 +46,7 @@ int gs_tiles_per_image(const gs_config* cfg, int* n) {
 
 int gs_proj_size(int B, int N, size_t* bytes) {
   if (B < 0 || N < 0 || !bytes) return GS_EINVAL;
-  *bytes = (sizeof(gs_record) + sizeof(int2)) * (size_t)B * (size_t)N;
+  *bytes = (sizeof(gs_record) + sizeof(int2) + sizeof(float2)) * (size_t)B * (size_t)N;
   return GS_OK;
 }
 

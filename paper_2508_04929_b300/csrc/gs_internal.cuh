@@ -14,6 +14,13 @@ constexpr int kGaussStride = 24;      // floats per activated Gaussian in the wo
 constexpr int kGradStride = 12;       // floats per Gaussian in the gradient accumulator
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kInv2Pi = 0.15915494309189535f;
+// Ill-conditioned splats -- row curvature a (log2 units per px^2) above kAThr, a conditional
+// standard deviation below 0.49 px, or a 2 x 2 covariance with (Sxx + Syy)^2 > kKappa det, a
+// condition number above about kKappa -- are stored as a completed square and rendered by
+// the exact path, which reads the low parts of the centre; gs_project writes those low parts
+// for them only.
+constexpr float kAThr = 3.f;
+constexpr float kKappa = 100.f;
 
 // Layout of the activated-Gaussian table (one row of kGaussStride floats per Gaussian).
 enum GaussField {

@@ -226,6 +226,7 @@ __global__ void k_activate(const float* __restrict__ theta, int N, float* __rest
   if (bad && j == 0) atomicOr(status, GS_STATUS_NONFINITE);
 }
 
+constexpr float kHalfLog2eP = 0.72134752044448170f;  // log2(e) / 2
 constexpr int kProjParticles = 16;  // particles per thread: one load of the Gaussian's row serves them all
 
 // One 32-byte store: the record fills its sector in a single request (proj 32-byte aligned).
@@ -239,7 +240,7 @@ __device__ __forceinline__ void st_record32(gs_record* dst, const gs_record& r) 
 template <bool kV8>
 __global__ void k_project(const float* __restrict__ gauss, int N, const float* __restrict__ Wall, int B, int D,
                           float inv_h, float kcut, gs_record* __restrict__ proj, int2* __restrict__ boxes,
-                          int* __restrict__ status) {
+                          float2* __restrict__ lo, int* __restrict__ status) {
   const int b0 = blockIdx.y * kProjParticles;
   __shared__ float Wsh[kProjParticles * 9];
   if (threadIdx.x < kProjParticles * 9 && b0 + (int)threadIdx.x / 9 < B)
@@ -297,17 +298,38 @@ __global__ void k_project(const float* __restrict__ gauss, int N, const float* _
     const float t2 = (Ws[6] * M[2] + Ws[7] * M[5] + Ws[8] * M[8]) * G[kInvS2 + 2];
     const float sqrt_det = G[kSprod] * sqrtf(t0 * t0 + t1 * t1 + t2 * t2);
     const float det = sqrt_det * sqrt_det;
-    const float wgt = __fdividef(G[kA] * kInv2Pi, sqrt_det);
-    const float k2 = __fdividef(-0.5f * kLog2e, det * inv_h * inv_h);
-    bad |= !(isfinite(wgt) && isfinite(k2) && sqrt_det > 0.f);
+    const float wgt = G[kA] * kInv2Pi / sqrt_det;
+    // A well-conditioned splat keeps the expanded form of Eq. 12's exponent (log2 units, pixel
+    // offsets): ca dx^2 + cb dx dy + cc dy^2 with (ca, cb, cc) = k2 (Syy, 2 Sxy, Sxx),
+    // k2 = -log2(e) / (2 det) (Sigma~ in px^2), and the linear weight w.  A thin or strongly
+    // anisotropic one (a > kAThr, or (Sxx + Syy)^2 > kKappa det, i.e. a condition number above
+    // about kKappa) is stored as the completed square -a (dx + r dy)^2 - q dy^2 with
+    // a = log2(e)/2 Syy / det, r = Sxy / Syy, q = log2(e)/2 / Syy, and log2 w.
+    const float ih2 = inv_h * inv_h;
+    const float k2 = -kHalfLog2eP / (det * ih2);
+    const float a = -k2 * Syy;
+    const bool exact = a > kAThr || (Sxx + Syy) * (Sxx + Syy) > kKappa * det;
+    float c1, c2, c3, c4;
+    if (!exact) {
+      c1 = k2 * Syy;
+      c2 = 2.f * k2 * Sxy;
+      c3 = k2 * Sxx;
+      c4 = wgt;
+    } else {
+      c1 = a;
+      c2 = Sxy / Syy;
+      c3 = -kHalfLog2eP / (Syy * ih2);
+      c4 = log2f(wgt);
+    }
+    bad |= !(isfinite(c1) && isfinite(c2) && isfinite(c3) && isfinite(c4) && isfinite(wgt) && sqrt_det > 0.f);
 
     gs_record r;
     r.cx = cx;
     r.cy = cy;
-    r.ca = k2 * Syy;
-    r.cb = 2.f * k2 * Sxy;
-    r.cc = k2 * Sxx;
-    r.w = wgt;
+    r.c1 = c1;
+    r.c2 = c2;
+    r.c3 = c3;
+    r.c4 = c4;
     r.x0 = 1; r.x1 = 0; r.y0 = 1; r.y1 = 0;
     if (!bad) {
       const float x0f = fmaxf(ceilf(__fsub_rn(cx, rx)), 0.f);
@@ -316,6 +338,16 @@ __global__ void k_project(const float* __restrict__ gauss, int N, const float* _
       const float y1f = fminf(floorf(__fadd_rn(cy, ry)), (float)(D - 1));
       if (x0f <= x1f && y0f <= y1f) {
         r.x0 = (int16_t)x0f; r.x1 = (int16_t)x1f; r.y0 = (int16_t)y0f; r.y1 = (int16_t)y1f;
+      }
+      // Ill-conditioned splats are rendered with the centre as a float-float: the low parts
+      // are the FP64 centre (exact products of the FP32 pose and mean) minus the FP32 one.
+      // Other records never read them, and they are not written.
+      if (exact) {
+        const double mx64 = ((double)Ws[0] * mux + (double)Ws[1] * muy) + (double)Ws[2] * muz;
+        const double my64 = ((double)Ws[3] * mux + (double)Ws[4] * muy) + (double)Ws[5] * muz;
+        const double c064 = (double)(D / 2), ih64 = (double)inv_h;
+        lo[(size_t)b * N + g] = make_float2((float)((mx64 * ih64 + c064) - (double)cx),
+                                            (float)((c064 - my64 * ih64) - (double)cy));
       }
     }
     any_bad |= bad;
@@ -347,10 +379,13 @@ cudaError_t launch_project(const gs_config& cfg, const float* gauss, int N, cons
   if (N <= 0 || B <= 0) return cudaSuccess;
   dim3 grid((N + 255) / 256, (B + kProjParticles - 1) / kProjParticles);
   int2* boxes = reinterpret_cast<int2*>(proj + (size_t)B * N);  // box plane after the B * N records
+  float2* lo = reinterpret_cast<float2*>(boxes + (size_t)B * N);  // then the centres' low parts
   if ((reinterpret_cast<uintptr_t>(proj) & 31) == 0)
-    k_project<true><<<grid, 256, 0, s>>>(gauss, N, W, B, cfg.D, inv_pixel(cfg), cfg.cutoff_sigma, proj, boxes, status);
+    k_project<true><<<grid, 256, 0, s>>>(gauss, N, W, B, cfg.D, inv_pixel(cfg), cfg.cutoff_sigma, proj, boxes, lo,
+                                         status);
   else
-    k_project<false><<<grid, 256, 0, s>>>(gauss, N, W, B, cfg.D, inv_pixel(cfg), cfg.cutoff_sigma, proj, boxes, status);
+    k_project<false><<<grid, 256, 0, s>>>(gauss, N, W, B, cfg.D, inv_pixel(cfg), cfg.cutoff_sigma, proj, boxes, lo,
+                                          status);
   return cudaGetLastError();
 }
 

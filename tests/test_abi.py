@@ -46,8 +46,8 @@ def test_host_side_validation_without_gpu():
     a = L.gs_workspace_size(L.config(64), 8, 2000, 0)
     b = L.gs_workspace_size(L.config(64), 8, 2000, 4096)
     assert b >= a + 4096 and a % 256 == 0
-    # gs_project's output: 32-byte records, then the 8-byte box plane
-    assert L.gs_proj_size(128, 100_000) == 128 * 100_000 * 40
+    # gs_project's output: 32-byte records, the 8-byte box plane, the 8-byte low-part plane
+    assert L.gs_proj_size(128, 100_000) == 128 * 100_000 * 48
     assert L.gs_proj_size(0, 10) == 0
     with pytest.raises(L.GsError):
         L.gs_proj_size(-1, 10)

@@ -137,6 +137,24 @@ def test_results_do_not_depend_on_tile_or_chunk(c1):
             assert rel_l2(o["dtheta"][:, sl], base["dtheta"][:, sl]) < 1e-5
 
 
+def test_tile_independence_with_ill_conditioned_splats():
+    """A batch mixing well- and ill-conditioned splats (both record forms, the exact path's
+    second pass): Q is still bitwise identical for every tile size and chunk depth."""
+    rng = synth.rng_for(5)
+    D, N, B = 64, 400, 3
+    th = synth.random_gaussians(N, D, rng)
+    sc = np.where(np.arange(N)[:, None] % 3 == 0, np.array([0.1, 8.0, 0.1]), np.exp(rng.uniform(-0.7, 1.1, (N, 3))))
+    th[:, 3:6] = synth.inv_softplus(sc / D)
+    Ws = synth.random_poses(B, rng)
+    ctf = synth.random_ctf(B, rng)
+    Y = synth.smooth_field(B, D, rng)
+    base = cuda_step(th, Ws, ctf, Y, D, tile=8)
+    assert 0 < int((base["rec"][:, :, 2] > 0).sum()) < B * N  # both forms present
+    for tile, chunk in ((16, 32), (16, 128), (32, 64)):
+        o = cuda_step(th, Ws, ctf, Y, D, tile=tile, chunk=chunk)
+        assert np.array_equal(o["Q"], base["Q"]), (tile, chunk)
+
+
 @pytest.mark.parametrize("D,tile", [(40, 16), (33, 8), (50, 32)])
 def test_ragged_and_odd_boxes(D, tile):
     th, Ws, ctf, Y = make_batch(3, D, 300, 3)
@@ -337,17 +355,15 @@ def test_wide_tile_grids(D, tile, mode):
     assert np.array_equal(rng_out.reshape(ranges.shape), ranges)
 
 
-EPS32 = 2.0 ** -24
 
-
-@pytest.mark.parametrize("ratio", [10, 40])
-def test_needles_and_pancakes(ratio):
-    """Strong anisotropy: needles (one axis of 8 px, two of 8 / ratio px) and pancakes (one thin
-    axis) in random orientations.  Boxes bit-exact.  The image's FP32 error grows with the
-    condition number kappa = ratio^2 of the 2 x 2 covariance (the exponent's expanded quadratic
-    form cancels), and the thin scale's gradient carries one more factor of the ratio: the bars
-    are max(1e-5, 2 eps kappa) for images and max(1e-3, 2 eps ratio^3) for gradients, eps = 2^-24.
-    The paper's workloads have ratios of at most 6."""
+@pytest.mark.parametrize("ratio", [10, 40, 160])
+@pytest.mark.parametrize("tile", [8, 16])
+def test_needles_and_pancakes(ratio, tile):
+    """Strong anisotropy: needles (one axis of 8 px, two of 8 / ratio px; at ratio 160 the thin
+    axes are 0.05 px) and pancakes (one thin axis) in random orientations.  Boxes bit-exact;
+    images within 1e-5 and gradients within 1e-3 per parameter group, the bars of every other
+    test.  Such splats are stored as a completed square with the centre as a float-float (their
+    expanded quadratic form would lose a factor of the 2 x 2 condition number, ratio^2)."""
     rng = synth.rng_for(77)
     D, N, B = 64, 60, 4
     th = synth.random_gaussians(N, D, rng)
@@ -360,7 +376,9 @@ def test_needles_and_pancakes(ratio):
                                               O.ctf_image(D, *[float(v) for v in ctf[b, 0:4]],
                                                           apix=float(ctf[b, 4]))) for b in range(B)]), 0.1, rng)
     ref = O.forward_backward(th, Ws, D, Y, ctf)
-    out = cuda_step(th, Ws, ctf, Y, D, tile=8)
+    out = cuda_step(th, Ws, ctf, Y, D, tile=tile)
+    if ratio >= 40:  # most of these splats take the completed-square form (third float > 0)
+        assert int((out["rec"][:, :, 2] > 0).sum()) > B * N // 3
     for b in range(B):
         x0, x1, y0, y1 = O.support_fp32(th, Ws[b], D)[:4]
         empty = (np.asarray(x0) > np.asarray(x1)) | (np.asarray(y0) > np.asarray(y1))
@@ -368,11 +386,10 @@ def test_needles_and_pancakes(ratio):
         assert np.array_equal(empty, box[:, 0] > box[:, 1])
         ok = ~empty
         assert np.array_equal(box[ok], np.stack([x0, x1, y0, y1], 1)[ok])
-        tol = max(1e-5, 2 * EPS32 * ratio ** 2)
-        assert rel_l2(out["Q"][b], ref["Q"][b]) < tol
-        assert rel_l2(out["X"][b], ref["X"][b]) < tol
+        assert rel_l2(out["Q"][b], ref["Q"][b]) < 1e-5
+        assert rel_l2(out["X"][b], ref["X"][b]) < 1e-5
     for name, sl in GROUPS:
-        assert rel_l2(out["dtheta"][:, sl], ref["dtheta"][:, sl]) < max(1e-3, 2 * EPS32 * ratio ** 3), name
+        assert rel_l2(out["dtheta"][:, sl], ref["dtheta"][:, sl]) < 1e-3, name
 
 
 def test_pair_overflow_is_reported_and_recovered(c1):
@@ -400,14 +417,14 @@ def test_invalid_arguments_raise():
     t = torch.zeros(10, 11, device=DEV)
     W = torch.zeros(2, 9, device=DEV)
     proj = torch.empty(L.gs_proj_size(2, 10), dtype=torch.uint8, device=DEV)
-    assert proj.numel() == 2 * 10 * (32 + 8)  # records, then the box plane
+    assert proj.numel() == 2 * 10 * (32 + 8 + 8)  # records, the box plane, the centres' low parts
     with pytest.raises(L.GsError):
         L.gs_project(L.config(64, tile=12), t, W, proj, torch.empty(1 << 20, dtype=torch.uint8, device=DEV))
     small_ws = torch.empty(256, dtype=torch.uint8, device=DEV)
     with pytest.raises(L.GsError) as e:
         L.gs_project(cfg, t, W, proj, small_ws)
     assert e.value.rc == L.GS_ENOSPC
-    with pytest.raises(ValueError):  # records only, without room for the box plane
+    with pytest.raises(ValueError):  # records only, without room for the planes that follow
         L.gs_project(cfg, t, W, torch.empty(2 * 10 * 32, dtype=torch.uint8, device=DEV),
                      torch.empty(1 << 20, dtype=torch.uint8, device=DEV))
 
