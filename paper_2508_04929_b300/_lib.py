@@ -126,7 +126,7 @@ def gs_tiles_per_image(cfg: GsConfig) -> int:
 
 
 def gs_proj_size(B: int, N: int) -> int:
-    """Bytes of gs_project's output buffer: B*N records, then the B*N-box plane."""
+    """Bytes of gs_project's output buffer: B*N records, the B*N-box plane, the B*N centre low parts."""
     n = _S()
     _check("gs_proj_size", lib.gs_proj_size(B, N, ctypes.byref(n)))
     return n.value
