@@ -36,8 +36,6 @@ from paper_2508_04929_b300 import synth  # noqa: E402
 
 METRIC = "fwd+bwd particle images/s at D=256,N=100k vs plain form; % of SFU-exp roofline"
 UNIT = "images/s"
-SM_COUNT = 148
-EX2_PER_CLK_PER_SM = 32  # measured on B300 by a throughput microbenchmark
 SM_MAX_MHZ = 2032.0
 CTF_SNR = 0.05
 # DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) per tile pair of one launch of
@@ -60,6 +58,14 @@ def step_kernels(D, tile):
             "k_render_fwd" + r, *ctf, "k_render_bwd" + r, "k_bwd_finalize", "k_adam", "k_count_step")
 
 
+class _NoDist:
+    """Single-process stand-in for torch.distributed in the dry run."""
+
+    @staticmethod
+    def all_reduce(t):
+        return t
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -76,9 +82,46 @@ def parse():
     p.add_argument("--mixed", type=int, default=1, help="also time the mixed-size batch (1/0)")
     p.add_argument("--cpu-sample", type=int, default=0, help="images in the CPU sample (0 = one per core, max 16)")
     p.add_argument("--dp", action="store_true",
-                   help="time a data-parallel training step (all-reduce of dL/dTheta before Adam) instead of "
-                        "independent replicas")
+                   help="time the data-parallel training step (all-reduce of dL/dTheta before Adam); the default "
+                        "when several ranks run")
+    p.add_argument("--replicas", action="store_true",
+                   help="with several ranks, time independent replicas (no collective) instead of the "
+                        "data-parallel step")
+    p.add_argument("--dry-run", action="store_true",
+                   help="exercise only the rank launch, the collective and the JSON line on the host (gloo, "
+                        "no GPU work); the line carries no measurement")
+    p.add_argument("--no-config2", action="store_true", help="skip the D=128, N=20k, B=64 batched-vs-plain line")
     return p.parse_args()
+
+
+def spawn_ranks(args):
+    """bench.py --gpus N (N > 1) started without a launcher: re-run it as N ranks under
+    torch.distributed.run on this node (127.0.0.1, a free port) and return the exit code."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr=127.0.0.1", f"--master-port={port}", os.path.abspath(__file__), *sys.argv[1:]]
+    return subprocess.call(cmd)
+
+
+def run_dry(args, rank, world, dist):
+    """The multi-rank plumbing without GPU work: each rank 'renders' its own particles (a host
+    array standing in for its part of dL/dTheta), the ranks all-reduce it as the data-parallel
+    step does, and rank 0 prints the JSON line with no measured value."""
+    import torch
+    g = torch.full((args.N, 11), float(rank + 1), dtype=torch.float32)
+    dist.all_reduce(g)
+    expect = world * (world + 1) / 2
+    ok = bool(torch.all(g == expect))
+    if rank == 0:
+        par = "replicas" if args.replicas else "dp"
+        print(json.dumps({"metric": METRIC, "value": None, "unit": UNIT, "n_gpus": world, "steps": 0,
+                          "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f32", "data": "dry run: no GPU work, nothing measured",
+                          "config": dict(workload(args), parallelism=par), "dry_run": {"allreduce_ok": ok}}),
+              flush=True)
 
 
 def workload(args):
@@ -138,6 +181,25 @@ def measure_h2d(torch, host, dev, reps=5):
     e1.record()
     torch.cuda.synchronize()
     return reps * host.numel() * host.element_size() / (e0.elapsed_time(e1) * 1e-3) / 1e9
+
+
+def measure_ex2_peak(torch, L, reps=5):
+    """ex2.approx throughput of this GPU (ex2/s), measured with the library's probe
+    (gs_probe_ex2: 8 independent ex2 chains per thread, 8 CTAs of 256 threads per SM): the
+    SFU-exp peak that the render kernels' roofline is quoted against."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sink = torch.zeros(1, dtype=torch.float32, device="cuda")
+    blocks, iters = 8 * sms, 4096
+    L.gs_probe_ex2(blocks, iters, sink)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    cnt = 0.0
+    for _ in range(reps):
+        cnt += L.gs_probe_ex2(blocks, iters, sink)
+    e1.record()
+    torch.cuda.synchronize()
+    return cnt / (e0.elapsed_time(e1) * 1e-3), sms
 
 
 def make_inputs(args, seed=0):
@@ -230,6 +292,95 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------
+# the plain form: one particle per launch sequence (batch size 1, as in the paper), Adam per image
+# ---------------------------------------------------------------------------------------
+def run_plain(args, L, torch, Splatter, t, W, C, Y, tile, chunk, dev, pairs_hint, nimg=None):
+    """Images/s of the plain per-image form, two ways: with the pair buffer sized up front
+    from the batch's mean pair count (x 2, no host sync per image), and with the buffer grown
+    on demand (gs_bin_sort's count read back to the host after every image)."""
+    nimg = min(args.B if nimg is None else nimg, 64)
+    out = {}
+    # each form twice, alternating, best of the two: the launch-bound plain form is sensitive to
+    # whatever else the host is doing
+    for name, grow in (("presized", False), ("grow_sync", True), ("presized", False), ("grow_sync", True)):
+        p1 = Splatter(Y.shape[-1], t.shape[0], 1, tile=tile, chunk=chunk, device=dev,
+                      pair_capacity=None if grow else 2 * pairs_hint + 4096)
+        th1 = t.clone()
+        m1, v1, g1 = torch.zeros_like(t), torch.zeros_like(t), torch.zeros_like(t)
+        for b in range(2):
+            g1.zero_()
+            p1.forward_backward(th1, W[b:b + 1], C[b:b + 1], Y[b:b + 1], g1, grow=grow, fused=True)
+        torch.cuda.synchronize()
+        s0 = time.perf_counter()
+        for b in range(nimg):
+            g1.zero_()
+            p1.forward_backward(th1, W[b:b + 1], C[b:b + 1], Y[b:b + 1], g1, grow=grow, fused=True)
+            L.gs_step(th1, g1, m1, v1, b + 1)
+        torch.cuda.synchronize()
+        rate = nimg / (time.perf_counter() - s0)
+        status = p1.status()
+        p1.close()
+        if not grow and status & L.GS_STATUS_OVERFLOW:
+            rate = None  # the pre-sized buffer was too small: no valid number
+        if rate is None or out.get(name, 0.0) is None:
+            out[name] = None
+        else:
+            out[name] = max(out.get(name, 0.0), rate)
+    return out
+
+
+# ---------------------------------------------------------------------------------------
+# the batched step against the plain form at D = 128, N = 20k, B = 64
+# ---------------------------------------------------------------------------------------
+def run_config2(args, L, torch, Splatter, dev, steps=10):
+    """The D = 128, N = 20,000, B = 64 configuration: the graph-captured batched step (tile and
+    chunk autotuned) against the plain per-image form on the same GPU."""
+    from paper_2508_04929_b300 import autotune
+    from paper_2508_04929_b300.batched import GraphStep, Problem
+    D, N, B = 128, 20_000, 64
+    rng = synth.rng_for(7)
+    t = torch.from_numpy(synth.random_gaussians(N, D, rng)).to(dev)
+    W = torch.from_numpy(synth.random_poses(B, rng).reshape(B, 9)).to(dev)
+    C = torch.from_numpy(synth.random_ctf(B, rng)).to(dev)
+    tg = torch.from_numpy(synth.random_gaussians(N, D, rng)).to(dev)
+    gt = Splatter(D, N, B, tile=16, chunk=128, device=dev)
+    _, X = gt.forward(tg, W, C)
+    sig = math.sqrt(float(X.double().var()) / 0.1)
+    gen = torch.Generator(device=dev).manual_seed(77)
+    Y = (X + sig * torch.randn(X.shape, device=dev, generator=gen)).contiguous()
+    gt.close()
+    tune = autotune.tune(D, N, B, t, W, C, Y, device=dev, tiles=(8, 16, 32), chunks=(64, 128))
+    prob = Problem(D=D, theta=t.clone(), W=W, ctf=C, Y=Y, tile=tune["tile"], chunk=tune["chunk"])
+    gs = GraphStep([prob], adam=True)
+    for _ in range(3):
+        gs.replay()
+    torch.cuda.synchronize()
+    st = gs.check()
+    n_pairs = int(prob.sp.n_pairs.item()) & 0xFFFFFFFF
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        gs.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    st |= gs.check()
+    ms = e0.elapsed_time(e1) / steps
+    gs.close()
+
+    class _A:  # the plain form's arguments at this size
+        pass
+    a = _A()
+    a.B = B
+    plain = run_plain(a, L, torch, Splatter, t, W, C, Y, tune["tile"], tune["chunk"], dev,
+                      pairs_hint=n_pairs // B)
+    batched = B / (ms * 1e-3)
+    return {"workload": f"D={D},N={N},B={B} synthetic particles, SNR 0.1", "tile": tune["tile"],
+            "chunk": tune["chunk"], "batched": batched, "batched_ms_per_step": ms, "plain": plain,
+            "speedup_vs_plain": batched / plain["presized"] if plain.get("presized") else None,
+            "status": st, "unit": UNIT}
 
 
 # ---------------------------------------------------------------------------------------
@@ -352,12 +503,24 @@ def run_reference(args, rank):
 # ---------------------------------------------------------------------------------------
 def main():
     args = parse()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(spawn_ranks(args))
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
         return
+    if args.dry_run:
+        import torch.distributed as dist
+        if world > 1:
+            dist.init_process_group("gloo")
+        run_dry(args, rank, world, dist if world > 1 else _NoDist())
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    # several ranks train one model by default: one all-reduce of dL/dTheta per step (DataParallelStep)
+    args.dp = args.dp or (world > 1 and not args.replicas)
     cores = cpu_cores()
     want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
     n_cpu = args.cpu_sample or min(cores, 16)
@@ -439,6 +602,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         ms_total = e0.elapsed_time(e1)
+        st_timed = gs.check()  # an overflow inside the timed steps would have dropped pairs
         restore()
         # the same kernels once more, eagerly, with CUDA events around the two render calls
         ev = {k: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for k in ("fwd", "bwd", "fft")}
@@ -470,22 +634,8 @@ def main():
     # --- plain form: one particle per launch sequence, batch size 1, Adam per image ---
     plain = None
     if not args.no_plain:
-        p1 = Splatter(args.D, args.N, 1, tile=tile, chunk=chunk, device=dev)
-        th1 = t.clone()
-        m1, v1, g1 = torch.zeros_like(t), torch.zeros_like(t), torch.zeros_like(t)
-        for b in range(2):
-            g1.zero_()
-            p1.forward_backward(th1, W[b:b + 1], C[b:b + 1], Y[b:b + 1], g1, grow=True, fused=True)
-        torch.cuda.synchronize()
-        nimg = min(args.B, 64)
-        s0 = time.perf_counter()
-        for b in range(nimg):
-            g1.zero_()
-            p1.forward_backward(th1, W[b:b + 1], C[b:b + 1], Y[b:b + 1], g1, grow=True, fused=True)
-            L.gs_step(th1, g1, m1, v1, b + 1)
-        torch.cuda.synchronize()
-        plain = nimg / (time.perf_counter() - s0)
-        p1.close()
+        plain = run_plain(args, L, torch, Splatter, t, W, C, Y, tile, chunk, dev,
+                          pairs_hint=n_pairs // max(args.B, 1))
 
     # --- end to end through the public API with host buffers: copy in, replay, loss out ---
     Yh = Y.cpu().pin_memory()
@@ -535,6 +685,7 @@ def main():
     done[pending].synchronize()
     host_losses += float(lossh[pending].sum())
     e2e = world * args.B * args.steps / (time.perf_counter() - s0)
+    st_e2e = gs.check()
     h2d_gbps = measure_h2d(torch, Yh, prob.Y)
     torch.cuda.synchronize()
     gs.close()
@@ -547,6 +698,14 @@ def main():
     if args.mixed:
         mixed = run_mixed(args, dev, torch)
 
+    # --- the D = 128, N = 20k, B = 64 configuration: batched step against the plain form ---
+    config2 = None
+    if not args.no_config2 and not args.no_plain and rank == 0:
+        config2 = run_config2(args, L, torch, Splatter, dev)
+
+    # --- the SFU-exp peak of this GPU, measured by the library's ex2 probe ---
+    peak_exp, sms = measure_ex2_peak(torch, L)
+
     cpu = None
     if pool is not None:
         Ynp = Y.cpu().numpy()
@@ -557,11 +716,12 @@ def main():
                "sample": f"{n} of the {args.B} particles (same inputs), one particle per process, "
                          f"median {statistics.median(per):.1f} s per particle"}
 
-    peak_exp = SM_COUNT * EX2_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6  # ex2 per second
     dom = "bwd" if t_bwd >= t_fwd else "fwd"
     t_dom = max(t_bwd, t_fwd)
     achieved = e_alg / (t_dom * 1e-3)
     clocks = clk.summary()
+    mhz = clocks["sm_mhz"] or SM_MAX_MHZ
+    ex2_per_clk = peak_exp / (sms * mhz * 1e6)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -569,19 +729,27 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(workload(args), tile=tile, chunk=chunk,
                            parallelism=("dp" if args.dp else "replicas") if world > 1 else ("dp1" if args.dp else "single")),
-            "plain_form": {"value": plain, "unit": UNIT, "form": "one particle per launch sequence, Adam per image"},
-            "speedup_vs_plain": (value / world / plain) if plain else None,
+            "plain_form": None if plain is None else {
+                "value": plain["presized"], "value_with_host_sync": plain["grow_sync"], "unit": UNIT,
+                "form": "one particle per launch sequence, Adam per image; value: pair buffer sized up front "
+                        "(no host sync per image); value_with_host_sync: pair count read back after every image"},
+            "speedup_vs_plain": (value / world / plain["presized"]) if plain and plain["presized"] else None,
+            "config2": config2,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "h2d_GBps": h2d_gbps, "h2d_bound": world * args.B / (h2d / (h2d_gbps * 1e9)),
                     "pipelining": "next step's host->device copy (into the other of two input slots of the captured step) overlaps the current step; a step's render starts before its images have arrived; every step's losses are copied back and read by the host one step later"},
             "gpu_launches": len(step_kernels(args.D, tile)) * args.steps,
             "roofline": {"bound": "alu", "kernel": f"k_render_{dom}", "achieved": achieved / 1e9,
                          "peak": peak_exp / 1e9, "unit": "Gex2/s", "frac": achieved / peak_exp,
-                         "traffic": render_traffic(dom, n_pairs), "peak_source": "measured ex2 rate x 148 SMs x max SM clock"},
+                         "traffic": render_traffic(dom, n_pairs),
+                         "peak_source": f"measured on this GPU by gs_probe_ex2: {ex2_per_clk:.2f} ex2/clk/SM x {sms} SMs "
+                                        f"at {mhz:.0f} MHz"},
             "fwd_bwd_splat": {"ms_fwd": t_fwd, "ms_bwd": t_bwd, "ms_ctf_loss_adjoint": t_ctf, "alg_evals_per_step": e_alg,
                               "pairs_per_step": n_pairs,
                               "frac_of_sfu_roofline": (2 * e_alg / ((t_fwd + t_bwd) * 1e-3)) / peak_exp},
-            "cpu_baseline": cpu, "clocks": clocks, "status": st,
+            "cpu_baseline": cpu, "clocks": clocks,
+            "status": st | st_timed | st_e2e,
+            "status_read": "after the warm-up, after the timed steps and after the end-to-end steps",
             "autotune": tune,
             "mixed_batch": mixed,
             "evaluation": evaluation,

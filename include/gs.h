@@ -50,6 +50,7 @@ enum {
   GS_EINVAL = 1,
   GS_ENOSPC = 2,
   GS_ECUDA = 3,
+  GS_ECAPTURE = 4, /* gs_bin_sort_noalloc: first call on a device made on a capturing stream */
 };
 
 /* Bits of the device status word (gs_read_status). */
@@ -267,8 +268,10 @@ int gs_step_counted(float* theta, const float* dtheta, float* m, float* v, int n
  * cudaFree or allocating library routine).  The scratch needed for (cfg, B, N) is written
  * to *scratch_needed (host, may be NULL); if it exceeds 8 MiB the call returns GS_ENOSPC
  * and does nothing else.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current) and caches it: make that first call
- * before capturing any stream.  All calls on a device share the array and leave their
+ * (cudaGetSymbolAddress, with that device current) and caches it; that look-up must not
+ * happen inside a stream capture, so a first call on a capturing stream returns GS_ECAPTURE
+ * before any other CUDA call (the capture is left untouched): make that first call before
+ * capturing any stream.  All calls on a device share the array and leave their
  * contents in it (the call clears what must start at zero); calls whose GPU work
  * overlaps -- on different streams without ordering -- race on the array.  Overflow of
  * pair_capacity is visible as *n_pairs > pair_capacity (the status word is internal).
@@ -426,6 +429,21 @@ int gs_fourier_shift(const gs_config* cfg, const float* in, const float* t, int 
  * keeps the parent's mass, mean and covariance.  Raw parameters (softplus inverted in FP64).
  * 0 <= alpha < 1; out != theta. */
 int gs_split_gaussians(const float* theta, int N, float alpha, float* out, gs_stream_t stream);
+
+/* -------------------------------------------------------------------------------------
+ * Diagnostics
+ * ------------------------------------------------------------------------------------- */
+
+/* gs_probe_ex2: launches a throughput probe of ex2.approx.ftz.f32, the special-function
+ * operation that each evaluated splat pixel takes in SumSplats (Algorithm 2) and its
+ * backward; the paper has no counterpart -- it measures the unit whose rate is the roofline
+ * of the render kernels on the GPU at hand.  blocks CTAs of 256 threads each run 8
+ * independent chains of `iters` steps x <- ex2(x) * s - 1 (bound by ex2, not by the FMA).
+ * The caller times the launch on `stream` (e.g. with CUDA events); *ex2_count (host, may be
+ * NULL) receives the number of ex2 the launch executes.  sink: one device float that is never
+ * written in practice (it keeps the chains from being optimized away).  GS_EINVAL for
+ * blocks outside [1, 2^20], iters outside [1, 2^24] or a NULL sink. */
+int gs_probe_ex2(int blocks, int iters, float* sink, gs_stream_t stream, double* ex2_count);
 
 #ifdef __cplusplus
 }

@@ -17,7 +17,7 @@ Notation follows the paper (arXiv 2508.04929):
   (the paper prints W; mu_dot = W mu forces the transpose), and the s / q chain of 3DGS
   written out explicitly (the paper defers it to 3DGS).
 
-Readings the paper leaves open (all listed in the design doc as well):
+Readings the paper leaves open:
 
 * Support: a Gaussian contributes to the pixels of the axis-aligned bounding box of its
   k-sigma ellipse, k = 3 by default (the paper inherits 3-sigma culling from the 3DGS

@@ -91,7 +91,7 @@ __global__ void k_split(const float* __restrict__ theta, int N, double alpha, fl
 
 int rc(cudaError_t e) { return e == cudaSuccess ? GS_OK : GS_ECUDA; }
 
-bool cfg_ok(const gs_config* c) { return c && c->D >= 1 && c->D <= 4096 && c->E > 0.f; }
+bool shift_cfg_ok(const gs_config* c) { return c && c->D >= 1 && c->D <= 4096 && c->E > 0.f; }
 
 }  // namespace
 }  // namespace gs
@@ -102,7 +102,7 @@ extern "C" {
 
 int gs_fourier_shift(const gs_config* cfg, const float* in, const float* t, int B, float* out, const gs_fft* fft,
                      void* ws, size_t ws_bytes, gs_stream_t stream) {
-  if (!cfg_ok(cfg) || B < 0 || B > 65535) return GS_EINVAL;
+  if (!shift_cfg_ok(cfg) || B < 0 || B > 65535) return GS_EINVAL;
   if (B == 0) return GS_OK;
   if (!in || !t || !out || !fft || !ws || ((uintptr_t)ws & 255) || in == out) return GS_EINVAL;
   if (fft->D != cfg->D || fft->B != B) return GS_EINVAL;

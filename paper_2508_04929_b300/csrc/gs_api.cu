@@ -11,26 +11,6 @@ namespace {
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
-bool cfg_ok(const gs_config* c) {
-  if (!c) return false;
-  if (c->D < 1 || c->D > 4096) return false;
-  if (!(c->tile == 8 || c->tile == 16 || c->tile == 32)) return false;
-  if (c->chunk < 32 || c->chunk > 512 || (c->chunk % 32) != 0) return false;
-  if (!(c->E > 0.f) || !isfinite(c->E)) return false;
-  if (!(c->cutoff_sigma > 0.f) || !isfinite(c->cutoff_sigma)) return false;
-  if (c->reduction != 0 && c->reduction != 1) return false;
-  const int ntx = (c->D + c->tile - 1) / c->tile;
-  if (ntx > 64) return false;
-  return true;
-}
-
-bool sizes_ok(const gs_config* c, int B, int N) {
-  if (B < 0 || N < 0 || B > 65535) return false;
-  const int ntx = (c->D + c->tile - 1) / c->tile;
-  if ((unsigned long long)N * (unsigned long long)(ntx * ntx) >= (1ull << 32)) return false;
-  return true;
-}
-
 int cuda_rc(cudaError_t e) { return e == cudaSuccess ? GS_OK : GS_ECUDA; }
 
 }  // namespace

@@ -11,8 +11,10 @@
 // pair list, tile ranges and pair count (outputs).
 //
 // The array's host-side name is not a device address, so the first call on each device
-// looks the address up with cudaGetSymbolAddress (with that device current) and caches it;
-// make that first call before capturing any stream.  Every call on a device shares the
+// looks the address up with cudaGetSymbolAddress (with that device current) and caches it.
+// That look-up may load the library's device code, which a stream capture must not see, so
+// a first call on a capturing stream is refused with GS_ECAPTURE before any other CUDA
+// call; make the first call before capturing.  Every call on a device shares the
 // array and leaves its contents behind; everything the kernels need to start at zero is
 // cleared by this call, but two calls whose work overlaps on the GPU (e.g. on two streams
 // without ordering between them) race on the array and give wrong results.
@@ -30,21 +32,22 @@ static __device__ __align__(256) unsigned char g_bin_scratch[kGsNoallocScratchBy
 std::mutex g_mutex;
 void* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of g_bin_scratch on the current device, looked up once per device.
-cudaError_t scratch_address(void** out) {
+// Device address of g_bin_scratch on the current device, looked up once per device.  A look-up
+// on a capturing stream is refused (GS_ECAPTURE) without touching the capture.
+int scratch_address(cudaStream_t s, void** out) {
   int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GS_ECUDA;
+  if (dev < 0 || dev >= kMaxDevices) return GS_ECUDA;
   std::lock_guard<std::mutex> lock(g_mutex);
   if (!g_scratch_addr[dev]) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return GS_ECAPTURE;
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_bin_scratch);
-    if (e != cudaSuccess) return e;
+    if (cudaGetSymbolAddress(&p, g_bin_scratch) != cudaSuccess) return GS_ECUDA;
     g_scratch_addr[dev] = p;
   }
   *out = g_scratch_addr[dev];
-  return cudaSuccess;
+  return GS_OK;
 }
 
 }  // namespace
@@ -53,12 +56,7 @@ extern "C" int gs_bin_sort_noalloc(const gs_config* cfg, const gs_record* proj, 
                                    uint32_t* pair_gauss, size_t pair_capacity, uint32_t* tile_ranges,
                                    uint32_t* n_pairs, gs_stream_t stream, size_t* scratch_needed) {
   using namespace gs;
-  if (!cfg || cfg->D < 1 || cfg->D > 4096 || !(cfg->tile == 8 || cfg->tile == 16 || cfg->tile == 32))
-    return GS_EINVAL;
-  if (cfg->chunk < 32 || cfg->chunk > 512 || (cfg->chunk % 32) != 0) return GS_EINVAL;
-  const int ntx = (cfg->D + cfg->tile - 1) / cfg->tile;
-  if (ntx > 64 || B < 0 || B > 65535 || N < 0) return GS_EINVAL;
-  if ((unsigned long long)N * (unsigned long long)(ntx * ntx) >= (1ull << 32)) return GS_EINVAL;
+  if (!cfg_ok(cfg) || !sizes_ok(cfg, B, N)) return GS_EINVAL;
   if (!n_pairs || (B > 0 && (!tile_ranges || (N > 0 && !proj)))) return GS_EINVAL;
   if (pair_capacity > 0 && !pair_gauss) return GS_EINVAL;
   if (pair_capacity > 0xffffffffull) pair_capacity = 0xffffffffull;
@@ -80,7 +78,8 @@ extern "C" int gs_bin_sort_noalloc(const gs_config* cfg, const gs_record* proj, 
   cudaStream_t s = (cudaStream_t)stream;
   if (B == 0) return cudaMemsetAsync(n_pairs, 0, sizeof(uint32_t), s) == cudaSuccess ? GS_OK : GS_ECUDA;
   void* scratch = nullptr;
-  if (scratch_address(&scratch) != cudaSuccess) return GS_ECUDA;
+  const int rc = scratch_address(s, &scratch);
+  if (rc != GS_OK) return rc;
   if (cudaMemsetAsync(scratch, 0, 256, s) != cudaSuccess) return GS_ECUDA;  // status word
   cudaError_t e = launch_bin(*cfg, L, proj, B, N, scratch, pair_gauss, pair_capacity, tile_ranges, n_pairs, s);
   return e == cudaSuccess ? GS_OK : GS_ECUDA;

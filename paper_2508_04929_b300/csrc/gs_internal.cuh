@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include "../../include/gs.h"
@@ -40,6 +41,27 @@ struct WsLayout {
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Argument checks shared by the entry points (host side).
+inline bool cfg_ok(const gs_config* c) {
+  if (!c) return false;
+  if (c->D < 1 || c->D > 4096) return false;
+  if (!(c->tile == 8 || c->tile == 16 || c->tile == 32)) return false;
+  if (c->chunk < 32 || c->chunk > 512 || (c->chunk % 32) != 0) return false;
+  if (!(c->E > 0.f) || !isfinite(c->E)) return false;
+  if (!(c->cutoff_sigma > 0.f) || !isfinite(c->cutoff_sigma)) return false;
+  if (c->reduction != 0 && c->reduction != 1) return false;
+  const int ntx = (c->D + c->tile - 1) / c->tile;
+  if (ntx > 64) return false;
+  return true;
+}
+
+inline bool sizes_ok(const gs_config* c, int B, int N) {
+  if (B < 0 || N < 0 || B > 65535) return false;
+  const int ntx = (c->D + c->tile - 1) / c->tile;
+  if ((unsigned long long)N * (unsigned long long)(ntx * ntx) >= (1ull << 32)) return false;
+  return true;
+}
 
 // CTAs per image of the D = 256 column kernel of gs_ctf_loss_grad (16 of the 129 columns
 // each) and the bytes of its loss partial sums and per-image tickets.

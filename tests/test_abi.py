@@ -51,3 +51,17 @@ def test_host_side_validation_without_gpu():
     assert L.gs_proj_size(0, 10) == 0
     with pytest.raises(L.GsError):
         L.gs_proj_size(-1, 10)
+
+
+def test_binding_rejects_host_tensors_without_gpu():
+    """Every device argument is checked before the call: a host (CPU) tensor raises
+    ValueError instead of handing the kernels a host pointer."""
+    torch = pytest.importorskip("torch")
+    from paper_2508_04929_b300 import _lib as L
+    cfg = L.config(64)
+    with pytest.raises(ValueError, match="CUDA device memory"):
+        L.gs_project(cfg, torch.zeros(10, 11), torch.zeros(2, 9), torch.zeros(1000, dtype=torch.uint8),
+                     torch.zeros(1000, dtype=torch.uint8))
+    with pytest.raises(ValueError, match="rows of 11"):
+        L.gs_project(cfg, torch.zeros(10, 12), torch.zeros(2, 9), None, None)
+

@@ -412,6 +412,26 @@ def test_pair_overflow_is_reported_and_recovered(c1):
     sp.close()
 
 
+def test_binding_validates_tensors():
+    """The binding checks dtype, device and contiguity before handing pointers to the
+    kernels: a float64 theta, a CPU theta and a transposed (strided) W each raise ValueError."""
+    cfg = L.config(64)
+    N, B = 10, 3
+    W = torch.zeros(B, 9, device=DEV)
+    proj = torch.empty(L.gs_proj_size(B, N), dtype=torch.uint8, device=DEV)
+    ws = torch.empty(L.gs_workspace_size(cfg, B, N), dtype=torch.uint8, device=DEV)
+    with pytest.raises(ValueError, match="float32"):
+        L.gs_project(cfg, torch.zeros(N, 11, dtype=torch.float64, device=DEV), W, proj, ws)
+    with pytest.raises(ValueError, match="CUDA device memory"):
+        L.gs_project(cfg, torch.zeros(N, 11), W, proj, ws)
+    with pytest.raises(ValueError, match="contiguous"):
+        L.gs_project(cfg, torch.zeros(N, 11, device=DEV), torch.zeros(9, B, device=DEV).t(), proj, ws)
+    with pytest.raises(ValueError, match="int32"):
+        L.gs_render_fwd(cfg, proj, N, torch.zeros(5, dtype=torch.int64, device=DEV),
+                        torch.zeros(16 * B * 2, dtype=torch.int32, device=DEV), B,
+                        torch.zeros(B, 64, 64, device=DEV))
+
+
 def test_invalid_arguments_raise():
     cfg = L.config(64)
     t = torch.zeros(10, 11, device=DEV)

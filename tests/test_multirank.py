@@ -88,3 +88,22 @@ def test_reference_arm_runs_on_rank_zero_only():
     env0 = dict(env1, RANK="0")
     p = subprocess.run([sys.executable, "-c", code], env=env0, capture_output=True, text=True, timeout=120)
     assert p.returncode == 3  # rank 0 starts the work (stopped here by the stub)
+
+
+def test_bench_starts_its_own_ranks_and_defaults_to_data_parallel():
+    """bench.py --gpus 2 without a launcher starts two ranks itself (torch.distributed.run on
+    127.0.0.1) and, with several ranks, times the data-parallel training step by default.  The
+    dry run exercises that launch and the collective on the host (gloo) and prints the JSON line
+    without a measurement."""
+    import json
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    env.pop("WORLD_SIZE", None)
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2", "--dry-run", "--D", "32",
+                          "--N", "200", "--B", "4"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr[-3000:]
+    lines = [json.loads(x) for x in out.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1  # rank 0 alone prints
+    line = lines[0]
+    assert line["n_gpus"] == 2 and line["config"]["parallelism"] == "dp"
+    assert line["dry_run"]["allreduce_ok"] and line["value"] is None
+

@@ -270,6 +270,32 @@ def test_tile_pairs_match_brute_force_enumeration():
     assert ranges[-1, -1, 1] == len(pg)
 
 
+@pytest.mark.parametrize("D,T", [(40, 8), (33, 16), (50, 32), (64, 8)])
+def test_tile_counts_match_brute_force_enumeration(D, T):
+    """tile_counts (the checker of the full-size GPU tests) equals, per (particle, tile), the
+    number of Gaussians with a pixel of their support box in that tile, found by enumerating
+    every box pixel; and equals the run lengths of tile_pairs.  Ragged D, boxes of several
+    tiles, and boxes clipped at every image edge (centres out to 0.6 D)."""
+    rng = synth.rng_for(19)
+    th = synth.random_gaussians(150, D, rng, centre_radius=0.6, scale_px=(0.5, 6.0))
+    Ws = synth.random_poses(3, rng)
+    got = O.tile_counts(th, Ws, D, T)
+    nt = -(-D // T)
+    expect = np.zeros((3, nt * nt), dtype=np.int64)
+    clipped = 0
+    for b in range(3):
+        x0, x1, y0, y1, _ = O.support_fp32(th, Ws[b], D)
+        for n in range(150):
+            tiles = {(i // T) * nt + (j // T) for i in range(y0[n], y1[n] + 1) for j in range(x0[n], x1[n] + 1)}
+            for t in tiles:
+                expect[b, t] += 1
+            clipped += int(x0[n] == 0 or y0[n] == 0 or x1[n] == D - 1 or y1[n] == D - 1)
+    assert clipped > 10 and expect.max() > 1
+    assert np.array_equal(got, expect)
+    _, ranges = O.tile_pairs(th, Ws, D, T)
+    assert np.array_equal(got, (ranges[:, :, 1] - ranges[:, :, 0]).astype(np.int64))
+
+
 def test_truncation_error_is_bounded_by_tail_mass():
     """The 3-sigma support only drops positive mass, at most the mass outside the box:
     P(|x| > 3 sigma_x) + P(|y| > 3 sigma_y) = 2 x 0.0027 per splat (plus sampling error)."""
