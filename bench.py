@@ -42,9 +42,9 @@ CTF_SNR = 0.05
 # each render kernel, from the capture summarised in profiles/render_kernels_d256_n100k_b64.md
 # (B = 64; the kernels read each pair's index and record once, so traffic scales with the pair
 # count).  Valid only for the gs_render.cu whose SHA-256 is recorded: otherwise null.
-RENDER_TRAFFIC = {"sha256": "6a4c04e970708d894f77b790d82b11d0ff960c93249a835ab7b26e497e6fad34",
-                  "bytes_per_pair": {"fwd": (306.627840e6 + 16.727552e6) / 25319264,
-                                     "bwd": (320.502784e6 + 3.731968e6) / 25319264}}
+RENDER_TRAFFIC = {"sha256": "66b5e8ecf3711fe447782c82950616bca6fdc9bc5152e7e743113e665a155408",
+                  "bytes_per_pair": {"fwd": (306.626560e6 + 16.579328e6) / 25319264,
+                                     "bwd": (320.590592e6 + 3.563776e6) / 25319264}}
 
 
 # libgs kernels launched by one graph-captured training step (cuFFT's and torch's gradient
