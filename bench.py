@@ -42,9 +42,9 @@ CTF_SNR = 0.05
 # each render kernel, from the capture summarised in profiles/render_kernels_d256_n100k_b64.md
 # (B = 64; the kernels read each pair's index and record once, so traffic scales with the pair
 # count).  Valid only for the gs_render.cu whose SHA-256 is recorded: otherwise null.
-RENDER_TRAFFIC = {"sha256": "66b5e8ecf3711fe447782c82950616bca6fdc9bc5152e7e743113e665a155408",
-                  "bytes_per_pair": {"fwd": (306.626560e6 + 16.579328e6) / 25319264,
-                                     "bwd": (320.590592e6 + 3.563776e6) / 25319264}}
+RENDER_TRAFFIC = {"sha256": "c199b1a061acf73a0c9459b9f0170aa28ab7be7715c32b14c952e4b657ba6ffc",
+                  "bytes_per_pair": {"fwd": (306.630912e6 + 16.534272e6) / 25319264,
+                                     "bwd": (320.534272e6 + 3.579136e6) / 25319264}}
 
 
 # libgs kernels launched by one graph-captured training step (cuFFT's and torch's gradient
@@ -605,13 +605,19 @@ def main():
         st_timed = gs.check()  # an overflow inside the timed steps would have dropped pairs
         restore()
         # the same kernels once more, eagerly, with CUDA events around the two render calls
-        ev = {k: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for k in ("fwd", "bwd", "fft")}
-        kt = {"fwd": [], "bwd": [], "fft": []}
+        ev = {k: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for k in ("proj", "bin", "fwd", "bwd", "fft")}
+        kt = {k: [] for k in ev}
         dth = torch.zeros_like(t)
         for _ in range(min(args.steps, 5)):
             dth.zero_()
+            torch.cuda._sleep(2_000_000)  # keeps the GPU busy while the host queues the parts below
+            ev["proj"][0].record(stream)
             sp.project(prob.theta, W)
+            ev["proj"][1].record(stream)
+            ev["bin"][0].record(stream)
             sp.bin_sort(grow=False)
+            ev["bin"][1].record(stream)
             ev["fwd"][0].record(stream)
             sp.render()
             ev["fwd"][1].record(stream)
@@ -630,6 +636,8 @@ def main():
     t_fwd = statistics.median(kt["fwd"])
     t_bwd = statistics.median(kt["bwd"])
     t_ctf = statistics.median(kt["fft"])
+    t_proj = statistics.median(kt["proj"])
+    t_bin = statistics.median(kt["bin"])
 
     # --- plain form: one particle per launch sequence, batch size 1, Adam per image ---
     plain = None
@@ -744,7 +752,8 @@ def main():
                          "traffic": render_traffic(dom, n_pairs),
                          "peak_source": f"measured on this GPU by gs_probe_ex2: {ex2_per_clk:.2f} ex2/clk/SM x {sms} SMs "
                                         f"at {mhz:.0f} MHz"},
-            "fwd_bwd_splat": {"ms_fwd": t_fwd, "ms_bwd": t_bwd, "ms_ctf_loss_adjoint": t_ctf, "alg_evals_per_step": e_alg,
+            "fwd_bwd_splat": {"ms_project": t_proj, "ms_bin_sort": t_bin, "ms_fwd": t_fwd, "ms_bwd": t_bwd,
+                              "ms_ctf_loss_adjoint": t_ctf, "alg_evals_per_step": e_alg,
                               "pairs_per_step": n_pairs,
                               "frac_of_sfu_roofline": (2 * e_alg / ((t_fwd + t_bwd) * 1e-3)) / peak_exp},
             "cpu_baseline": cpu, "clocks": clocks,

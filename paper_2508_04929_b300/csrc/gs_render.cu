@@ -327,6 +327,17 @@ __device__ __forceinline__ void store_block(const u64 (&acc)[kB][4], float* __re
   }
 }
 
+// The block of a tile whose list is empty: zeros, in the layout store_block writes.
+__device__ __forceinline__ void store_zero_block(float* __restrict__ Q, int b, int D, int X, int Y) {
+  const int lane = threadIdx.x & 31;
+  const int i = Y + (lane >> 2), j = X + 2 * (lane & 3);
+  if (i < D) {
+    float* row = Q + ((size_t)b * D + i) * D;
+    if (j < D) row[j] = 0.f;
+    if (j + 1 < D) row[j + 1] = 0.f;
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // Backward of one item: the six moment sums in (t, dy).
 // g2[u][rp] holds dL/dQ at (column u, rows 2 rp, 2 rp + 1).
@@ -607,6 +618,10 @@ __global__ void __launch_bounds__(kTileWarps * 32, kFwd8MinBlocks) k_render_fwd8
   const int X = (tile % ntx) * kB, Y = (tile / ntx) * kB;
   const size_t rr = ((size_t)b * ntx * ntx + tile) * 2;
   const uint32_t start = ranges[rr], end = ranges[rr + 1];
+  if (start >= end) {  // warp-uniform: no Gaussian touches the block
+    store_zero_block(Q, b, D, X, Y);
+    return;
+  }
   const float4* pr = reinterpret_cast<const float4*>(proj + (size_t)b * N);
   const float2* lo = lo_all + (size_t)b * N;
   const uint32_t gmax = (uint32_t)N - 1u;  // pair entries are clamped: a bad list cannot leave proj
@@ -802,6 +817,10 @@ __global__ void __launch_bounds__(kRegionWarps * 32) k_render_fwd16(const gs_rec
   const int X = reg.RX + (warp & 1) * kB, Y = reg.RY + (warp >> 1) * kB;
   const size_t rr = ((size_t)b * ntx * ntx + tile) * 2;
   const uint32_t start = ranges[rr], end = ranges[rr + 1];
+  if (start >= end) {  // uniform over the CTA: no Gaussian touches the region
+    store_zero_block(Q, b, D, X, Y);
+    return;
+  }
   const size_t pbase = (size_t)b * N;
   const float2* lo = lo_all + pbase;
   u64 acc[kB][4];
