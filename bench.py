@@ -42,9 +42,9 @@ CTF_SNR = 0.05
 # each render kernel, from the capture summarised in profiles/render_kernels_d256_n100k_b64.md
 # (B = 64; the kernels read each pair's index and record once, so traffic scales with the pair
 # count).  Valid only for the gs_render.cu whose SHA-256 is recorded: otherwise null.
-RENDER_TRAFFIC = {"sha256": "c199b1a061acf73a0c9459b9f0170aa28ab7be7715c32b14c952e4b657ba6ffc",
-                  "bytes_per_pair": {"fwd": (306.630912e6 + 16.534272e6) / 25319264,
-                                     "bwd": (320.534272e6 + 3.579136e6) / 25319264}}
+RENDER_TRAFFIC = {"sha256": "1744410d1f3913910f5752efe7e142735fa7b1a6823497ea13f3f1da30fb616d",
+                  "bytes_per_pair": {"fwd": (306.636544e6 + 16.469504e6) / 25319264,
+                                     "bwd": (320.559616e6 + 3.130112e6) / 25319264}}
 
 
 # libgs kernels launched by one graph-captured training step (cuFFT's and torch's gradient

@@ -630,32 +630,35 @@ __global__ void __launch_bounds__(kTileWarps * 32, kFwd8MinBlocks) k_render_fwd8
   for (int u = 0; u < kB; ++u)
 #pragma unroll
     for (int rp = 0; rp < 4; ++rp) acc[u][rp] = 0ull;
-  // record of the current item in (na, nb) with its Gaussian g0; Gaussian indices of the next
-  // three in g1, g2, g3; the record two items ahead is prefetched into L1 so that its load one
-  // item ahead hits there
+  // record of the current item in (na, nb); list entries (Gaussian indices) of the next three
+  // in g1, g2, g3, kept as loaded and clamped only where used, so that nothing waits on a list
+  // load before its use three items later (a clamp next to the load would stall the warp for
+  // the load's full latency every item); the record two items ahead is prefetched into L1 so
+  // that its load one item ahead hits there
   uint32_t i = start + lane;
   float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na;
-  uint32_t g0 = 0, g1 = 0, g2 = 0, g3 = 0;
+  uint32_t g1 = 0, g2 = 0, g3 = 0;
   bool any_exact = false;
   if (i < end) {
-    g0 = min(pair_gauss[i], gmax);
+    const uint32_t g0 = min(pair_gauss[i], gmax);
     na = __ldg(pr + 2 * (size_t)g0);
     nb = __ldg(pr + 2 * (size_t)g0 + 1);
   }
-  if (i + 32 < end) g1 = min(pair_gauss[i + 32], gmax);
-  if (i + 64 < end) g2 = min(pair_gauss[i + 64], gmax);
-  if (i + 64 < end) asm volatile("prefetch.global.L1 [%0];" ::"l"(pr + 2 * (size_t)g2));
-  if (i + 96 < end) g3 = min(pair_gauss[i + 96], gmax);
+  if (i + 32 < end) g1 = pair_gauss[i + 32];
+  if (i + 64 < end) g2 = pair_gauss[i + 64];
+  if (i + 64 < end) asm volatile("prefetch.global.L1 [%0];" ::"l"(pr + 2 * (size_t)min(g2, gmax)));
+  if (i + 96 < end) g3 = pair_gauss[i + 96];
   while (i < end) {
     const float4 ca = na, cb = nb;
     i += 32;
     if (i < end) {
-      na = __ldg(pr + 2 * (size_t)g1);
-      nb = __ldg(pr + 2 * (size_t)g1 + 1);
-      if (i + 64 < end) asm volatile("prefetch.global.L1 [%0];" ::"l"(pr + 2 * (size_t)g3));
+      const uint32_t gc = min(g1, gmax);
+      na = __ldg(pr + 2 * (size_t)gc);
+      nb = __ldg(pr + 2 * (size_t)gc + 1);
+      if (i + 64 < end) asm volatile("prefetch.global.L1 [%0];" ::"l"(pr + 2 * (size_t)min(g3, gmax)));
       g1 = g2;
       g2 = g3;
-      if (i + 96 < end) g3 = min(pair_gauss[i + 96], gmax);
+      if (i + 96 < end) g3 = pair_gauss[i + 96];
     }
     if (!exact_record(ca))
       fwd_fast_record(ca, cb, X, Y, acc);
@@ -702,6 +705,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, kBwd8MinBlocks) k_render_bwd8
   const float2* lo = lo_all + (size_t)b * N;
   const uint32_t gmax = (uint32_t)N - 1u;  // pair entries are clamped: a bad list cannot leave proj / wacc
   float pacc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  // list entries are kept as loaded and clamped where used (see k_render_fwd8)
   uint32_t i = start + lane;
   float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na;
   uint32_t g0 = 0, g1 = 0;
@@ -711,16 +715,16 @@ __global__ void __launch_bounds__(kTileWarps * 32, kBwd8MinBlocks) k_render_bwd8
     na = __ldg(pr + 2 * (size_t)g0);
     nb = __ldg(pr + 2 * (size_t)g0 + 1);
   }
-  if (i + 32 < end) g1 = min(pair_gauss[i + 32], gmax);
+  if (i + 32 < end) g1 = pair_gauss[i + 32];
   while (i < end) {
     const float4 ca = na, cb = nb;
     const uint32_t g = g0;
     i += 32;
     if (i < end) {
-      g0 = g1;
+      g0 = min(g1, gmax);
       na = __ldg(pr + 2 * (size_t)g0);
       nb = __ldg(pr + 2 * (size_t)g0 + 1);
-      if (i + 32 < end) g1 = min(pair_gauss[i + 32], gmax);
+      if (i + 32 < end) g1 = pair_gauss[i + 32];
     }
     if (!exact_record(ca))
       bwd_fast_pair<kPose>(ca, cb, g, X, Y, g2, W, h, kap, wacc, gauss, pacc);
