@@ -297,6 +297,13 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------
 # the plain form: one particle per launch sequence (batch size 1, as in the paper), Adam per image
 # ---------------------------------------------------------------------------------------
+def best_plain(plain):
+    """The faster of the plain form's two measured variants (None if neither has a number): the
+    speedups divide by it, so that the baseline is the best the per-image form achieved."""
+    vals = [v for v in (plain or {}).values() if v]
+    return max(vals) if vals else None
+
+
 def run_plain(args, L, torch, Splatter, t, W, C, Y, tile, chunk, dev, pairs_hint, nimg=None):
     """Images/s of the plain per-image form, two ways: with the pair buffer sized up front
     from the batch's mean pair count (x 2, no host sync per image), and with the buffer grown
@@ -379,7 +386,7 @@ def run_config2(args, L, torch, Splatter, dev, steps=10):
     batched = B / (ms * 1e-3)
     return {"workload": f"D={D},N={N},B={B} synthetic particles, SNR 0.1", "tile": tune["tile"],
             "chunk": tune["chunk"], "batched": batched, "batched_ms_per_step": ms, "plain": plain,
-            "speedup_vs_plain": batched / plain["presized"] if plain.get("presized") else None,
+            "speedup_vs_plain": batched / best_plain(plain) if best_plain(plain) else None,
             "status": st, "unit": UNIT}
 
 
@@ -738,10 +745,12 @@ def main():
             "config": dict(workload(args), tile=tile, chunk=chunk,
                            parallelism=("dp" if args.dp else "replicas") if world > 1 else ("dp1" if args.dp else "single")),
             "plain_form": None if plain is None else {
-                "value": plain["presized"], "value_with_host_sync": plain["grow_sync"], "unit": UNIT,
-                "form": "one particle per launch sequence, Adam per image; value: pair buffer sized up front "
-                        "(no host sync per image); value_with_host_sync: pair count read back after every image"},
-            "speedup_vs_plain": (value / world / plain["presized"]) if plain and plain["presized"] else None,
+                "value": best_plain(plain), "presized": plain["presized"], "value_with_host_sync": plain["grow_sync"],
+                "unit": UNIT,
+                "form": "one particle per launch sequence, Adam per image; presized: pair buffer sized up front "
+                        "(no host sync per image); value_with_host_sync: pair count read back after every image; "
+                        "value: the faster of the two"},
+            "speedup_vs_plain": (value / world / best_plain(plain)) if plain and best_plain(plain) else None,
             "config2": config2,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "h2d_GBps": h2d_gbps, "h2d_bound": world * args.B / (h2d / (h2d_gbps * 1e9)),
