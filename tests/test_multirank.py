@@ -107,3 +107,17 @@ def test_bench_starts_its_own_ranks_and_defaults_to_data_parallel():
     assert line["n_gpus"] == 2 and line["config"]["parallelism"] == "dp"
     assert line["dry_run"]["allreduce_ok"] and line["value"] is None
 
+
+
+def test_plain_baseline_is_the_faster_variant():
+    """The speedups divide by the faster of the plain form's two measured variants, so that the
+    baseline is the best the per-image form achieved; a variant without a number is ignored."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    assert bench.best_plain({"presized": 2480.0, "grow_sync": 2774.0}) == 2774.0
+    assert bench.best_plain({"presized": 7354.0, "grow_sync": 5828.0}) == 7354.0
+    assert bench.best_plain({"presized": None, "grow_sync": 5828.0}) == 5828.0
+    assert bench.best_plain({"presized": None, "grow_sync": None}) is None
+    assert bench.best_plain(None) is None
