@@ -656,19 +656,20 @@ def main():
     Yh = Y.cpu().pin_memory()
     Wh = W.cpu().pin_memory()
     Ch = C.cpu().pin_memory()
-    lossh = [torch.empty(args.B, dtype=torch.float32).pin_memory() for _ in range(2)]
+    # Each step's inputs are copied from pinned host memory into one of three input slots of the
+    # graph-captured step while earlier steps run, and the step replays that slot's graphs: the
+    # front half (projection, binning, render) waits only for the poses, so on the first step it
+    # starts while the images are still being copied in.  Each step's losses come back to pinned
+    # host memory; the host reads them two steps later, after enqueueing the steps in between, so
+    # that neither a slow host nor a late copy leaves the GPU waiting.  (The data-parallel step is
+    # fed through the static buffers, one step behind.)
+    depth = 1 if args.dp else 2  # steps the host runs ahead of the losses it reads
+    lossh = [torch.empty(args.B, dtype=torch.float32).pin_memory() for _ in range(depth + 1)]
     h2d = Yh.numel() * 4 + Wh.numel() * 4 + Ch.numel() * 4
     d2h = lossh[0].numel() * 4
-    # every step copies its own inputs from pinned host memory (double-buffered: the next
-    # step's copy overlaps the current step) and reads its per-image losses back to the host
-    # Each step's inputs are copied from pinned host memory into one of two input slots of the
-    # graph-captured step while the previous step runs, and the step replays that slot's graphs:
-    # the front half (projection, binning, render) waits only for the poses, so on the first
-    # step it starts while the images are still being copied in.  Each step's losses come back
-    # to pinned host memory; the host reads them one step later, after enqueueing the next
-    # step, so that the GPU never waits for the host.  (The data-parallel step is fed through
-    # the static buffers.)
     from paper_2508_04929_b300.batched import HostFeeder, SlotFeeder
+    if not args.dp:
+        gs.record_slots(depth + 1)
     feeder = HostFeeder(gs) if args.dp else SlotFeeder(gs)
     if not args.dp:  # two untimed fed steps: the slot graphs' first launches are not part of the rate
         for _ in range(2):
@@ -676,29 +677,33 @@ def main():
             feeder.step()
         torch.cuda.synchronize()
     restore()
-    done = [torch.cuda.Event(), torch.cuda.Event()]
+    done = [torch.cuda.Event() for _ in range(depth + 1)]
     host_losses = 0.0
     torch.cuda.synchronize()
     s0 = time.perf_counter()
-    feeder.prefetch(Wh, Ch, Yh)
-    pending = None
+    ahead = 1 if args.dp else min(depth, args.steps)  # steps whose inputs are in flight before the first replay
+    for _ in range(ahead):
+        feeder.prefetch(Wh, Ch, Yh)
+    read = 0
     for i in range(args.steps):
         if args.dp:
             feeder.load()
-        if i + 1 < args.steps:
+        if i + ahead < args.steps:
             feeder.prefetch(Wh, Ch, Yh)
         if args.dp:
             step()
         else:
             feeder.step()
-        lossh[i % 2].copy_(prob.sp.loss[: args.B], non_blocking=True)
-        done[i % 2].record()
-        if pending is not None:
-            done[pending].synchronize()  # the host has the previous step's losses
-            host_losses += float(lossh[pending].sum())
-        pending = i % 2
-    done[pending].synchronize()
-    host_losses += float(lossh[pending].sum())
+        lossh[i % (depth + 1)].copy_(prob.sp.loss[: args.B], non_blocking=True)
+        done[i % (depth + 1)].record()
+        if i - read >= depth:  # the host reads the losses of the step `depth` steps back
+            done[read % (depth + 1)].synchronize()
+            host_losses += float(lossh[read % (depth + 1)].sum())
+            read += 1
+    while read < args.steps:
+        done[read % (depth + 1)].synchronize()
+        host_losses += float(lossh[read % (depth + 1)].sum())
+        read += 1
     e2e = world * args.B * args.steps / (time.perf_counter() - s0)
     st_e2e = gs.check()
     h2d_gbps = measure_h2d(torch, Yh, prob.Y)
@@ -754,7 +759,7 @@ def main():
             "config2": config2,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "h2d_GBps": h2d_gbps, "h2d_bound": world * args.B / (h2d / (h2d_gbps * 1e9)),
-                    "pipelining": "next step's host->device copy (into the other of two input slots of the captured step) overlaps the current step; a step's render starts before its images have arrived; every step's losses are copied back and read by the host one step later"},
+                    "pipelining": "each step's host->device copy (into one of three input slots of the captured step) runs while earlier steps do; a step's render starts before its images have arrived; every step's losses are copied back and read by the host two steps later"},
             "gpu_launches": len(step_kernels(args.D, tile)) * args.steps,
             "roofline": {"bound": "alu", "kernel": f"k_render_{dom}", "achieved": achieved / 1e9,
                          "peak": peak_exp / 1e9, "unit": "Gex2/s", "frac": achieved / peak_exp,
